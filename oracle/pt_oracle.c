@@ -1,0 +1,342 @@
+/*
+ * pt_oracle.c -- plain, slow CPU oracle for predicate transfer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no source with the CUDA library: the
+ * structs below are declared here independently of the public header.
+ *
+ * What it computes (Yang, Zhao, Yu, Koutris, "Predicate Transfer", CIDR'24):
+ *   - filter transformation (Section 3.2, "Filter Transformation", Fig. 2):
+ *     a table is scanned once; rows that pass the local predicate and every
+ *     incoming filter survive, and their outgoing join keys are inserted
+ *     into one fresh outgoing filter per outgoing edge;
+ *   - the predicate transfer graph (Section 3.2, "Predicate Transfer
+ *     Graph"): every join edge points from the smaller table to the bigger;
+ *   - the schedule (Section 3.2, "Transfer Schedule", Fig. 3): a forward
+ *     pass in topological order, then a backward pass over the reversed
+ *     edges whose input is the forward survivors;
+ *   - "Filter Type" (Section 3.2): with precise filters (exact key sets) a
+ *     transfer is a semi-join; mode exact=1 runs that schedule.
+ *
+ * The paper fixes no hash, filter layout, filter size or number of bits.
+ * This library fixes them as follows (the same definitions, written
+ * separately, are what the CUDA path implements):
+ *   key:    int32 is sign-extended to 64 bits, int64 taken as is (u64).
+ *   hash:   H(x) = mix(x ^ seed + G), H(a, b) = mix(H(a) ^ b), with G and
+ *           mix() the SplitMix64 increment and output function (Steele,
+ *           Lea, Flood, OOPSLA 2014).
+ *   filter: nblocks blocks of B bits (B = 256 or 512) stored as uint32
+ *           words, block j = words [j*B/32, (j+1)*B/32), bit t of a block
+ *           = bit (t & 31) of its word t >> 5.
+ *   bits:   block j = ((h >> 32) * nblocks) >> 32; with lo = low 32 bits
+ *           of h, h1 = lo mod B, h2 = (lo >> 16) | 1, bit i = (h1 + i*h2)
+ *           mod B for i < k (Kirsch-Mitzenmacher double hashing, 2006).
+ *   size:   nblocks = max(1, ceil(min(c, n_probe) * bits_per_key / B)),
+ *           c = the building visit's survivor count, n_probe = rows of the
+ *           table on the other end of the edge.
+ *   order:  tables are ranked by (rows, table id); the forward pass visits
+ *           them in ascending rank, the backward pass in descending rank.
+ *   probe:  incoming filters are probed in ascending c_b / n_b (survivors
+ *           of the building visit over its table's rows), ties by edge id
+ *           (LIP-style ordering, Section 3.2); the order never changes a
+ *           result, only how many key sectors are read.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int64_t n_rows;
+    int32_t n_cols;
+    const void* const* cols;   /* n_cols column base pointers */
+    const int32_t* dtypes;     /* 0 = int32, 1 = int64 */
+    const uint32_t* sel;       /* selection bitmap, NULL = every row */
+} o_table;
+
+typedef struct {
+    int32_t t0, ncols, c0[2], t1, c1[2];
+    uint32_t flags;
+} o_edge;
+
+typedef struct {
+    int32_t bits_per_key, k, block_bits;
+    int32_t pad_;
+    uint64_t seed;
+} o_cfg;
+
+#define O_SPLITMIX_GAMMA 0x9E3779B97F4A7C15ULL
+
+/* ---- hash ------------------------------------------------------------- */
+
+static uint64_t o_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t o_key(const void* col, int32_t dtype, int64_t row) {
+    if (dtype == 0) {
+        int64_t v = ((const int32_t*)col)[row]; /* sign extension */
+        return (uint64_t)v;
+    }
+    return (uint64_t)((const int64_t*)col)[row];
+}
+
+uint64_t o_hash1(uint64_t x, uint64_t seed) { return o_mix((x ^ seed) + O_SPLITMIX_GAMMA); }
+
+uint64_t o_hash2(uint64_t a, uint64_t b, uint64_t seed) { return o_mix(o_hash1(a, seed) ^ b); }
+
+/* ---- blocked Bloom filter -------------------------------------------- */
+
+int64_t o_nblocks(int64_t c, int64_t n_probe, int32_t bits_per_key, int32_t block_bits) {
+    int64_t n_est = c < n_probe ? c : n_probe;
+    int64_t nb = (n_est * bits_per_key + block_bits - 1) / block_bits;
+    return nb < 1 ? 1 : nb;
+}
+
+int64_t o_block_of(uint64_t h, int64_t nblocks) {
+    return (int64_t)(((h >> 32) * (uint64_t)nblocks) >> 32);
+}
+
+void o_bits_of(uint64_t h, int32_t block_bits, int32_t k, int32_t* pos) {
+    uint32_t lo = (uint32_t)h;
+    uint32_t h1 = lo & (uint32_t)(block_bits - 1);
+    uint32_t h2 = (lo >> 16) | 1u;
+    for (int32_t i = 0; i < k; i++) pos[i] = (int32_t)((h1 + (uint32_t)i * h2) & (uint32_t)(block_bits - 1));
+}
+
+void o_filter_insert(uint32_t* words, int64_t nblocks, int32_t block_bits, int32_t k, uint64_t h) {
+    int32_t pos[64];
+    int64_t base = o_block_of(h, nblocks) * (block_bits / 32);
+    o_bits_of(h, block_bits, k, pos);
+    for (int32_t i = 0; i < k; i++) words[base + (pos[i] >> 5)] |= 1u << (pos[i] & 31);
+}
+
+int o_filter_probe(const uint32_t* words, int64_t nblocks, int32_t block_bits, int32_t k, uint64_t h) {
+    int32_t pos[64];
+    int64_t base = o_block_of(h, nblocks) * (block_bits / 32);
+    o_bits_of(h, block_bits, k, pos);
+    for (int32_t i = 0; i < k; i++)
+        if (!((words[base + (pos[i] >> 5)] >> (pos[i] & 31)) & 1u)) return 0;
+    return 1;
+}
+
+/* ---- predicate transfer graph and order (Section 3.2) ---------------- */
+
+static int o_rank_less(const int64_t* n_rows, int32_t a, int32_t b) {
+    if (n_rows[a] != n_rows[b]) return n_rows[a] < n_rows[b];
+    return a < b;
+}
+
+/* src[e]/dst[e]: forward orientation of edge e (smaller table -> bigger).
+ * order[]: tables in ascending rank, a topological order of that DAG.    */
+int o_orient(int32_t n_tables, const int64_t* n_rows, int32_t n_edges, const o_edge* e,
+             int32_t* src, int32_t* dst, int32_t* order) {
+    for (int32_t i = 0; i < n_edges; i++) {
+        if (o_rank_less(n_rows, e[i].t0, e[i].t1)) { src[i] = e[i].t0; dst[i] = e[i].t1; }
+        else { src[i] = e[i].t1; dst[i] = e[i].t0; }
+    }
+    for (int32_t i = 0; i < n_tables; i++) order[i] = i;
+    for (int32_t i = 1; i < n_tables; i++) {      /* insertion sort by rank */
+        int32_t x = order[i], j = i - 1;
+        while (j >= 0 && o_rank_less(n_rows, x, order[j])) { order[j + 1] = order[j]; j--; }
+        order[j + 1] = x;
+    }
+    return 0;
+}
+
+/* ---- exact key sets (precise filters, Section 3.2 "Filter Type") ----- */
+
+typedef struct { uint64_t a, b; } o_pair;
+
+static int o_pair_cmp(const void* x, const void* y) {
+    const o_pair* p = (const o_pair*)x;
+    const o_pair* q = (const o_pair*)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return 0;
+}
+
+/* ---- one visit's key on one side of an edge -------------------------- */
+
+static void o_side(const o_edge* e, int32_t table, const int32_t** cols) {
+    *cols = (e->t0 == table) ? e->c0 : e->c1;
+}
+
+static o_pair o_edge_key(const o_table* t, const o_edge* e, int32_t table, int64_t row) {
+    const int32_t* c;
+    o_pair p;
+    o_side(e, table, &c);
+    p.a = o_key(t->cols[c[0]], t->dtypes[c[0]], row);
+    p.b = e->ncols == 2 ? o_key(t->cols[c[1]], t->dtypes[c[1]], row) : 0;
+    return p;
+}
+
+static uint64_t o_edge_hash(const o_table* t, const o_edge* e, int32_t table, int64_t row, uint64_t seed) {
+    o_pair p = o_edge_key(t, e, table, row);
+    return e->ncols == 2 ? o_hash2(p.a, p.b, seed) : o_hash1(p.a, seed);
+}
+
+static int o_bit(const uint32_t* bm, int64_t r) { return (int)((bm[r >> 5] >> (r & 31)) & 1u); }
+
+/* number of 32-byte sectors of a column of width w bytes that hold a row
+ * whose flag is set (row r lives in sector (r * w) / 32)                 */
+static int64_t o_sectors(const unsigned char* flag, int64_t n, int32_t w) {
+    int64_t per = 32 / w, cnt = 0;
+    for (int64_t s = 0; s * per < n; s++) {
+        int any = 0;
+        for (int64_t r = s * per; r < (s + 1) * per && r < n; r++) any |= flag[r];
+        cnt += any;
+    }
+    return cnt;
+}
+
+/*
+ * o_transfer: the full forward + backward predicate transfer.
+ *
+ * surv[p*n_tables + v]  (caller-owned, ceil(n_v/32) words): survivors of
+ *                       table v after pass p (0 = forward, 1 = backward).
+ * count[p*n_tables + v]: popcount of that bitmap.
+ * filt[p*n_edges + e]   (Bloom mode; caller-owned, at least
+ *                       o_nblocks(min(n_t0, n_t1), ...) * B/32 words):
+ *                       the filter built on edge e in pass p.
+ * nblocks[p*n_edges+e]: its size in blocks (0 in exact mode).
+ * sectors[(p*n_tables + v)*2 + {0,1}] (nullable): key-column sectors read
+ *                       by the probes (each probed column, sectors with a
+ *                       row still alive when its edge is probed) and by the
+ *                       builds (each distinct build column, sectors with a
+ *                       survivor).
+ * Returns 0, or -1 on invalid input.
+ */
+int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge* e,
+               const o_cfg* cfg, int32_t exact, uint32_t* const* surv, int64_t* count,
+               uint32_t* const* filt, int64_t* nblocks, int64_t* sectors) {
+    int32_t B = cfg->block_bits, K = cfg->k, wpb = cfg->block_bits / 32;
+    int32_t v, p, i, j;
+
+    if (B != 256 && B != 512) return -1;
+    if (K < 1 || K > 16 || cfg->bits_per_key < 1) return -1;
+    for (i = 0; i < n_edges; i++) {
+        if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return -1;
+        if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return -1;
+    }
+
+    int64_t* n_rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_tables > 0 ? n_tables : 1));
+    int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    int32_t* dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_tables + 1));
+    int32_t* ine = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    o_pair** set = (o_pair**)calloc((size_t)(2 * n_edges + 1), sizeof(o_pair*));
+    int64_t* set_n = (int64_t*)calloc((size_t)(2 * n_edges + 1), sizeof(int64_t));
+
+    for (v = 0; v < n_tables; v++) n_rows[v] = t[v].n_rows;
+    o_orient(n_tables, n_rows, n_edges, e, src, dst, order);
+
+    for (p = 0; p < 2; p++) {
+        for (int32_t oi = 0; oi < n_tables; oi++) {
+            /* forward: ascending rank; backward: reversed edges, descending rank */
+            v = p == 0 ? order[oi] : order[n_tables - 1 - oi];
+            int64_t n = n_rows[v];
+            const uint32_t* in = p == 0 ? t[v].sel : surv[v];  /* backward starts from forward survivors */
+            uint32_t* out = surv[p * n_tables + v];
+            unsigned char* alive = (unsigned char*)malloc((size_t)(n > 0 ? n : 1));
+            int64_t c = 0, probe_sec = 0, build_sec = 0;
+
+            for (int64_t r = 0; r < n; r++) alive[r] = in ? (unsigned char)o_bit(in, r) : 1;
+
+            /* incoming edges of v in this pass, in LIP order */
+            int32_t n_in = 0;
+            for (i = 0; i < n_edges; i++) {
+                int32_t into = p == 0 ? dst[i] : src[i];
+                if (into == v) ine[n_in++] = i;
+            }
+            for (i = 1; i < n_in; i++) {
+                int32_t x = ine[i];
+                j = i - 1;
+                while (j >= 0) {
+                    int32_t y = ine[j];
+                    int32_t bx = p == 0 ? src[x] : dst[x], by = p == 0 ? src[y] : dst[y];
+                    uint64_t lhs = (uint64_t)count[p * n_tables + bx] * (uint64_t)n_rows[by];
+                    uint64_t rhs = (uint64_t)count[p * n_tables + by] * (uint64_t)n_rows[bx];
+                    if (lhs < rhs || (lhs == rhs && x < y)) { ine[j + 1] = ine[j]; j--; }
+                    else break;
+                }
+                ine[j + 1] = x;
+            }
+
+            /* probe: a row survives iff it is in the input and every incoming filter accepts its key */
+            for (i = 0; i < n_in; i++) {
+                const o_edge* ed = &e[ine[i]];
+                const int32_t* cs;
+                o_side(ed, v, &cs);
+                for (j = 0; j < ed->ncols; j++)
+                    probe_sec += o_sectors(alive, n, t[v].dtypes[cs[j]] == 0 ? 4 : 8);
+                for (int64_t r = 0; r < n; r++) {
+                    if (!alive[r]) continue;
+                    if (exact) {
+                        o_pair key = o_edge_key(&t[v], ed, v, r);
+                        o_pair* s = set[p * n_edges + ine[i]];
+                        int64_t sn = set_n[p * n_edges + ine[i]];
+                        alive[r] = sn > 0 && bsearch(&key, s, (size_t)sn, sizeof(o_pair), o_pair_cmp) != NULL;
+                    } else {
+                        uint64_t h = o_edge_hash(&t[v], ed, v, r, cfg->seed);
+                        alive[r] = (unsigned char)o_filter_probe(filt[p * n_edges + ine[i]],
+                                                                 nblocks[p * n_edges + ine[i]], B, K, h);
+                    }
+                }
+            }
+
+            /* survivor bitmap, tail bits zero */
+            for (int64_t w = 0; w < (n + 31) / 32; w++) out[w] = 0;
+            for (int64_t r = 0; r < n; r++)
+                if (alive[r]) { out[r >> 5] |= 1u << (r & 31); c++; }
+            count[p * n_tables + v] = c;
+
+            /* build one fresh outgoing filter per outgoing edge from the survivors' keys */
+            int32_t seen_cols[64];
+            int32_t n_seen = 0;
+            for (i = 0; i < n_edges; i++) {
+                int32_t from = p == 0 ? src[i] : dst[i];
+                if (from != v) continue;
+                const o_edge* ed = &e[i];
+                const int32_t* cs;
+                o_side(ed, v, &cs);
+                for (j = 0; j < ed->ncols; j++) {
+                    int32_t k2, dup = 0;
+                    for (k2 = 0; k2 < n_seen; k2++) dup |= seen_cols[k2] == cs[j];
+                    if (!dup && n_seen < 64) {
+                        seen_cols[n_seen++] = cs[j];
+                        build_sec += o_sectors(alive, n, t[v].dtypes[cs[j]] == 0 ? 4 : 8);
+                    }
+                }
+                int32_t other = ed->t0 == v ? ed->t1 : ed->t0;
+                if (exact) {
+                    o_pair* s = (o_pair*)malloc(sizeof(o_pair) * (size_t)(c > 0 ? c : 1));
+                    int64_t m = 0;
+                    for (int64_t r = 0; r < n; r++)
+                        if (alive[r]) s[m++] = o_edge_key(&t[v], ed, v, r);
+                    qsort(s, (size_t)m, sizeof(o_pair), o_pair_cmp);
+                    set[p * n_edges + i] = s;
+                    set_n[p * n_edges + i] = m;
+                    nblocks[p * n_edges + i] = 0;
+                } else {
+                    int64_t nb = o_nblocks(c, n_rows[other], cfg->bits_per_key, B);
+                    uint32_t* f = filt[p * n_edges + i];
+                    memset(f, 0, sizeof(uint32_t) * (size_t)(nb * wpb));
+                    for (int64_t r = 0; r < n; r++)
+                        if (alive[r]) o_filter_insert(f, nb, B, K, o_edge_hash(&t[v], ed, v, r, cfg->seed));
+                    nblocks[p * n_edges + i] = nb;
+                }
+            }
+            if (sectors) {
+                sectors[(p * n_tables + v) * 2 + 0] = probe_sec;
+                sectors[(p * n_tables + v) * 2 + 1] = build_sec;
+            }
+            free(alive);
+        }
+    }
+    for (i = 0; i < 2 * n_edges; i++) free(set[i]);
+    free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(ine);
+    return 0;
+}
