@@ -1,0 +1,410 @@
+"""Benchmark: forward + backward predicate transfer on one B300.
+
+Workload (default): the 6-table snowflake at 10x (fact 60M rows, mid 15M,
+dim2 2M, dim1 1.5M, dim3 100k, a 25-row table), int64 keys, a two-column
+composite key on the fact->mid edge, Zipf(1.1)-skewed fact foreign keys,
+predicates keeping 10% / 1% / 30% of dim1 / dim2 / dim3, Bloom filters of
+16 bits per key (k = 4, 256-bit blocks).  Synthetic data (seeded), a
+stand-in for TPC-H at scale factor 10.
+
+One step = pt_run_forward + pt_run_backward over every table (both passes
+of the paper's Section 3.2 schedule).  Metric: transfer rows/s = rows of
+every visited table summed over both passes / step time.  Inputs are
+resident in HBM when the timed region starts; the working set (~2.3 GB)
+is far larger than L2 (126 MB), so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (the paper's engine is a single-core CPU program; the oracle is
+its stand-in here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FALLBACK_HBM_GBS = 6400.0
+NOMINAL_HBM_GBS = 8000.0
+
+
+def make_workload(name: str, bpk: int):
+    if name == "snowflake_x10":
+        return W.snowflake(scale=10, int64=True, composite=True, zipf=1.1, bits_per_key=bpk)
+    if name == "snowflake":
+        return W.snowflake(scale=1, bits_per_key=bpk)
+    if name == "cyclic5":
+        return W.cyclic5(bits_per_key=bpk)
+    if name == "chain3":
+        return W.chain3(bits_per_key=bpk)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_desc(w) -> dict:
+    return {
+        "workload": w.name,
+        "tables": {t.name: t.n_rows for t in w.tables},
+        "key_dtypes": sorted({str(c.dtype) for t in w.tables for c in t.cols}),
+        "edges": len(w.edges),
+        "bits_per_key": w.bits_per_key, "k": w.k, "block_bits": w.block_bits,
+        "passes": "forward+backward",
+        "l2": f"inputs larger than L2 (working set {w.nbytes() / 1e9:.2f} GB vs 126 MB), no flush",
+    }
+
+
+def visit_rows(w) -> int:
+    return 2 * sum(t.n_rows for t in w.tables)
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                return json.load(f)
+        except Exception:
+            return {}
+    return {}
+
+
+def hbm_peak() -> tuple:
+    pk = measured_peaks()
+    for key in ("hbm_gbs", "hbm_copy_gbs", "hbm"):
+        if key in pk and isinstance(pk[key], (int, float)):
+            return float(pk[key]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_timing(w, budget_s: float) -> dict:
+    import oracle
+    oracle.build()
+    rows = visit_rows(w)
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        oracle.transfer(w)
+        runs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": rows * runs / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full forward+backward transfer(s) of {w.name} ({rows} visit rows each), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.bpk)
+    rows = visit_rows(w)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; its first run is already timed like the rest
+    import oracle
+    oracle.build()
+    # each step: one oracle transfer of the full workload (a few seconds on one core)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.transfer(w)
+    dt = time.perf_counter() - t0
+    value = rows * args.steps / dt
+    line = {"impl": "reference", "metric": "transfer rows/s", "value": value, "unit": "rows/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": workload_desc(w),
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full transfers of {w.name} on one host core"},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pt_kernels.cu", "pt_internal.h"):
+        with open(os.path.join(ROOT, "paper_2307_15255_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload: str, bpk: int):
+    """Per-launch DRAM bytes of the scan kernel from a committed ncu summary,
+    or None when none exists for this kernel source."""
+    p = os.path.join(ROOT, "profiles", "scan_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    key = f"{workload}_b{bpk}"
+    ent = d.get("per_workload", {}).get(key)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+def ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("gloo")
+
+    from paper_2307_15255_b300 import pt as P
+    from paper_2307_15255_b300.session import TransferSession
+
+    w = make_workload(args.workload, args.bpk)
+    rows = visit_rows(w)
+    tables_dev = []
+    for t in w.tables:
+        cols = [torch.from_numpy(c).cuda() for c in t.cols]
+        sel = None if t.sel is None else torch.from_numpy(t.sel.view(np.int32)).cuda()
+        tables_dev.append((t.n_rows, cols, sel))
+    edges = [(e.t0, e.c0, e.t1, e.c1) for e in w.edges]
+    stream = torch.cuda.Stream()
+    launch = tuple(args.launch) if args.launch else None
+    s = TransferSession(tables_dev, edges, w.bits_per_key, w.k, w.block_bits, w.seed, stream=stream,
+                        launch=launch)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        s.run()
+    torch.cuda.synchronize()
+
+    # accounting of one run (identical every step: same inputs)
+    acc = {"bitmap": 0, "probe_keys": 0, "build_keys": 0, "ids": 0, "filters": 0}
+    scan_bytes = 0
+    for p in range(2):
+        for v, t in enumerate(w.tables):
+            st = s.stats(p, v)
+            nw = (t.n_rows + 31) // 32
+            bm = 4 * nw * (2 if st["has_input_bitmap"] else 1)
+            acc["bitmap"] += bm
+            acc["probe_keys"] += 32 * st["probe_sectors"]
+            acc["build_keys"] += 32 * st["build_sectors"]
+            ids = 8 * st["survivors"] if st["n_out"] > 0 else 0
+            acc["ids"] += ids
+            acc["filters"] += st["filter_bytes"]
+            scan_bytes += bm + 32 * st["probe_sectors"] + ids // 2
+    alg_bytes = sum(acc.values())
+
+    # timed region: direct launches, scan kernels bracketed by CUDA events on the session stream
+    P.pt_set_kernel_timing(s.ctx, True)
+    launches0 = P.pt_get_launch_count(s.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = P.pt_get_launch_count(s.ctx) - launches0
+    kt = P.pt_get_kernel_time(s.ctx)
+    P.pt_set_kernel_timing(s.ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # the same transfer replayed from a CUDA graph (no events inside)
+    P.pt_set_graph_mode(s.ctx, True)
+    s.run()
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        s.run()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+    P.pt_set_graph_mode(s.ctx, False)
+
+    # end to end through the C ABI from pinned host buffers: H2D of every
+    # column and selection, both passes, D2H of every final survivor bitmap
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        h2d = 0
+        for t in w.tables:
+            cols = [torch.from_numpy(c).pin_memory() for c in t.cols]
+            sel = None if t.sel is None else torch.from_numpy(t.sel.view(np.int32)).pin_memory()
+            h2d += sum(c.numel() * c.element_size() for c in cols) + (0 if sel is None else sel.numel() * 4)
+            host.append((cols, sel))
+        outs = [torch.empty(max((t.n_rows + 31) // 32, 1), dtype=torch.int32).pin_memory() for t in w.tables]
+        d2h = sum(((t.n_rows + 31) // 32) * 4 + 8 for t in w.tables)
+        se = TransferSession([(t.n_rows, c, sl) for t, (c, sl) in zip(w.tables, host)], edges, w.bits_per_key,
+                             w.k, w.block_bits, w.seed, stream=stream, launch=launch)
+        n_e2e = max(1, min(args.steps, 5))
+        se.run()
+        for v in range(w.n_tables):
+            P.pt_get_survivors(se.ctx, v, outs[v].data_ptr())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for v, (cols, sel) in enumerate(host):
+                se.update(v, cols, sel)
+            se.run()
+            for v in range(w.n_tables):
+                P.pt_get_survivors(se.ctx, v, outs[v].data_ptr())
+        dt = (time.perf_counter() - t0) / n_e2e
+        barrier()
+        se.close()
+        e2e = {"value": rows * world / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n_e2e}
+
+    s.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = hbm_peak()
+    scan_launches = max(kt["scan_launches"], 1)
+    scan_ms_per_launch = kt["scan_ms"] / scan_launches
+    visits_per_step = 2 * w.n_tables
+    achieved = (scan_bytes / visits_per_step) / (scan_ms_per_launch * 1e-3) / 1e9
+    traffic = committed_traffic(args.workload, args.bpk)
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_timing(w, args.cpu_seconds)
+    line = {
+        "metric": "transfer rows/s",
+        "value": rows * world / (ms * 1e-3),
+        "unit": "rows/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded star/snowflake generator; stands in for TPC-H SF10)",
+        "config": workload_desc(w),
+        "hbm": {"alg_bytes_per_step": alg_bytes, "alg_breakdown": acc,
+                "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                "frac_of_peak": alg_bytes / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak, "peak_kind": peak_kind,
+                "frac_of_nominal_8tbs": alg_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
+        "roofline": {"kernel": "pt_scan_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "alg_bytes_per_launch": scan_bytes / visits_per_step,
+                     "ms_per_launch": scan_ms_per_launch, "launches_timed": kt["scan_launches"]},
+        "graph_ms_per_step": graph_ms,
+        "graph_value": rows * world / (graph_ms * 1e-3),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "scale_mode": "replicas" if world > 1 else "single",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="snowflake_x10")
+    ap.add_argument("--bpk", type=int, default=16)
+    ap.add_argument("--launch", type=int, nargs=3, metavar=("THREADS", "SMEM", "CTAS_PER_SM"))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

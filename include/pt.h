@@ -1,0 +1,228 @@
+/*
+ * pt.h -- C ABI of the B300 predicate-transfer library (libpt.so).
+ *
+ * Predicate transfer (Yang, Zhao, Yu, Koutris, "Predicate Transfer:
+ * Efficient Pre-Filtering on Multi-Join Queries", CIDR 2024) pre-filters
+ * the tables of a multi-join query before the joins run.  Each table is a
+ * vertex of the join graph, each equi-join an edge (Section 3.1).  Edges
+ * are pointed from the smaller table to the bigger one (Section 3.2,
+ * "Predicate Transfer Graph"); a forward pass visits the tables in
+ * topological order and a backward pass repeats it over the reversed edges
+ * (Section 3.2, "Transfer Schedule", Fig. 3).  Visiting a table scans its
+ * join-key columns once: a row survives if its local predicate holds (a
+ * selection bitmap here) and every incoming Bloom filter accepts its key;
+ * the survivors' keys are inserted into one new Bloom filter per outgoing
+ * edge (Section 3.2, "Filter Transformation", Fig. 2).
+ *
+ * Everything a run computes is done by CUDA kernels on one GPU; there is
+ * no CPU fallback.  All functions return a pt_status; none throws.  On an
+ * error, pt_last_error() holds a one-line message.  Device work is
+ * enqueued on the context's stream and is asynchronous unless a function
+ * says otherwise; errors of asynchronous work surface at the next call
+ * that synchronizes (pt_get_*).
+ *
+ * Filter specification (the paper names Apache Arrow's filter but fixes
+ * no layout; this library fixes one):
+ *   key     int32 values are sign-extended to 64 bits; int64 taken as is.
+ *   hash    H(x) = mix(x ^ seed + 0x9E3779B97F4A7C15) with mix() the
+ *           SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014);
+ *           a two-column key hashes as H(a, b) = mix(H(a) ^ b).
+ *   layout  nblocks blocks of block_bits (256 or 512) bits, stored as
+ *           uint32 words; block j is words [j*block_bits/32, ...), bit t of
+ *           a block is bit (t & 31) of word (t >> 5) of the block.
+ *   bits    block j = ((h >> 32) * nblocks) >> 32; with lo = (uint32)h,
+ *           h1 = lo mod block_bits, h2 = (lo >> 16) | 1, a key sets bits
+ *           (h1 + i*h2) mod block_bits for i = 0 .. k-1.
+ *   size    nblocks = max(1, ceil(min(c, n_probe) * bits_per_key /
+ *           block_bits)), c = survivors of the visit that builds the
+ *           filter, n_probe = rows of the table at the edge's other end.
+ * Bitmaps are uint32[ceil(n/32)]: row r is bit (r & 31) of word r >> 5;
+ * bits at and beyond n are zero in every bitmap the library writes.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_INVALID = 1,     /* bad argument, malformed graph, out-of-range id */
+    PT_ERR_OOM = 2,         /* device or host allocation failed */
+    PT_ERR_CUDA = 3,        /* a CUDA call failed (message in pt_last_error) */
+    PT_ERR_STATE = 4,       /* call out of order (e.g. run before pt_plan) */
+    PT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    PT_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} pt_status;
+
+typedef enum { PT_I32 = 0, PT_I64 = 1 } pt_dtype;
+
+/* where a buffer passed to the library lives */
+typedef enum { PT_MEM_DEVICE = 0, PT_MEM_HOST = 1 } pt_mem;
+
+typedef struct {
+    int32_t bits_per_key; /* 1..64; bits of filter per expected key */
+    int32_t k;            /* 1..16; bits set per key */
+    int32_t block_bits;   /* 256 or 512 */
+    int32_t reserved;     /* must be 0 */
+    uint64_t seed;        /* hash seed, XORed into every key */
+} pt_filter_cfg;
+
+typedef struct {
+    const void* data; /* n_rows values; device pointer (PT_MEM_DEVICE, borrowed,
+                         must stay valid and unchanged while runs use it) or
+                         host pointer (PT_MEM_HOST, copied in; pinned memory
+                         makes the copy asynchronous) */
+    int32_t dtype;    /* pt_dtype */
+    int32_t mem;      /* pt_mem */
+} pt_column;
+
+/* An equi-join t0.c0[i] = t1.c1[i] for i < ncols (ncols = 1, or 2 for a
+ * composite key).  Column indexes refer to pt_register_table's list.
+ * flags must be 0 (one-direction edges are not implemented). */
+typedef struct {
+    int32_t t0;
+    int32_t ncols;
+    int32_t c0[2];
+    int32_t t1;
+    int32_t c1[2];
+    uint32_t flags;
+} pt_edge;
+
+/* Per-visit accounting, read back after a pass (see pt_get_visit_stats). */
+typedef struct {
+    int64_t n_rows;
+    int64_t survivors;     /* popcount of the visit's survivor bitmap */
+    int64_t probe_sectors; /* 32-byte key sectors read by the probes: per probed
+                              column, sectors holding a row still alive when
+                              that column's edge is probed */
+    int64_t build_sectors; /* per distinct build column, sectors holding a survivor */
+    int64_t filter_bytes;  /* bytes of the outgoing filters built by the visit */
+    int32_t n_in;          /* incoming edges in this pass */
+    int32_t n_out;         /* outgoing edges in this pass */
+    int32_t has_input_bitmap;
+    int32_t reserved;
+} pt_visit_stats;
+
+/* Version of this ABI: (major << 16) | minor. */
+uint32_t pt_abi_version(void);
+
+/* Create a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t that all device work of the context is enqueued on; NULL
+ * makes the context create (and own) a non-blocking stream.  cfg is
+ * copied.  Errors: PT_ERR_INVALID (cfg out of range), PT_ERR_CUDA. */
+pt_status pt_create(pt_ctx** out, const pt_filter_cfg* cfg, void* cuda_stream);
+
+/* Free every buffer the context owns (filters, bitmaps, row ids, copies of
+ * host columns) after waiting for its stream.  NULL is a no-op. */
+pt_status pt_destroy(pt_ctx* ctx);
+
+/* Register a table (a vertex of the join graph, Section 3.1): n_rows rows
+ * (0 <= n_rows < 2^31) and n_cols (1..16) key columns.  sel is the local
+ * predicate's result as a bitmap (layout above) in memory sel_mem, or NULL
+ * for "every row".  Device buffers are borrowed; host buffers are copied to
+ * library-owned device memory on the context's stream.  *table_id receives
+ * ids 0, 1, 2 ... in registration order.  Only before pt_plan. */
+pt_status pt_register_table(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_column* cols,
+                            const uint32_t* sel, int32_t sel_mem, int32_t* table_id);
+
+/* Replace the column data and selection of a registered table (same n_rows,
+ * same column count and dtypes).  Host buffers are copied again on the
+ * context's stream; device buffers are re-borrowed.  Allowed after pt_plan:
+ * the next run uses the new data. */
+pt_status pt_update_table(pt_ctx* ctx, int32_t table_id, const pt_column* cols, const uint32_t* sel,
+                          int32_t sel_mem);
+
+/* Set the join graph: n_edges (0..64) equi-join edges.  Both sides of an
+ * edge need the same number of columns; int32 and int64 columns may be
+ * joined (values compare after sign extension).  Only before pt_plan. */
+pt_status pt_set_join_graph(pt_ctx* ctx, int32_t n_edges, const pt_edge* edges);
+
+/* Build the transfer schedule (Section 3.2): each edge points from the
+ * table with fewer rows to the one with more (ties: lower table id first),
+ * which makes a DAG; tables are visited in ascending (rows, id) order in the
+ * forward pass and in the reverse order in the backward pass.  Allocates
+ * all device memory a run needs.  order_out (nullable, n_tables entries)
+ * receives the forward visiting order; mem_bytes_out (nullable) the bytes
+ * of device memory allocated.  Errors: PT_ERR_OOM, PT_ERR_INVALID. */
+pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out);
+
+/* Forward pass: visit every table in topological order of the transfer
+ * graph; a visit's input is its selection bitmap.  Asynchronous. */
+pt_status pt_run_forward(pt_ctx* ctx);
+
+/* Backward pass over the reversed edges; a visit's input is the table's
+ * forward survivors (Section 3.2, Fig. 3).  Requires a completed
+ * pt_run_forward since the last pt_update_table.  Asynchronous. */
+pt_status pt_run_backward(pt_ctx* ctx);
+
+/* pt_run_forward then pt_run_backward as one call.  When the context's
+ * graph mode is on (pt_set_graph_mode), the first call captures both
+ * passes into a CUDA graph and later calls replay it. */
+pt_status pt_run_transfer(pt_ctx* ctx);
+
+/* 1 = capture the transfer into a CUDA graph on first pt_run_transfer and
+ * replay it afterwards; 0 = launch kernels directly (default). */
+pt_status pt_set_graph_mode(pt_ctx* ctx, int32_t on);
+
+/* Copy the survivors of table_id after the last completed pass (backward
+ * if it ran, else forward) into bitmap_out (ceil(n/32) words, host or
+ * device memory) and their number into *count_out (either pointer may be
+ * NULL).  Synchronizes the context's stream. */
+pt_status pt_get_survivors(pt_ctx* ctx, int32_t table_id, uint32_t* bitmap_out, int64_t* count_out);
+
+/* Same for a given pass (0 = forward, 1 = backward). */
+pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uint32_t* bitmap_out,
+                                int64_t* count_out);
+
+/* Copy the filter built on edge edge_id in pass (0/1) into words_out
+ * (nblocks*block_bits/32 words, host or device; NULL = size only) and its
+ * size in blocks into *nblocks_out.  Synchronizes the context's stream. */
+pt_status pt_get_filter(pt_ctx* ctx, int32_t pass, int32_t edge_id, uint32_t* words_out,
+                        int64_t* nblocks_out);
+
+/* Accounting of one visit of the last run of that pass.  Synchronizes. */
+pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_visit_stats* out);
+
+/* Launch shape of the scan kernel: threads per CTA (128..1024, multiple of
+ * 32), shared-memory filter budget per CTA in bytes (0 = probe every filter
+ * from L2), and CTAs per SM to aim for (0 = as many as fit).  Takes effect
+ * at the next run; invalidates a captured graph. */
+pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm);
+
+/* Kernel timing.  pt_set_kernel_timing(ctx, 1) starts recording CUDA
+ * events on the context's stream around every scan (probe + compact)
+ * launch and around every visit's size/clear + insert pair (or, in graph
+ * mode, around each graph launch); pt_get_kernel_time returns the summed
+ * milliseconds and launch counts since timing was last switched on or off.
+ * Synchronizes the context's stream. */
+pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on);
+pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
+                             int32_t* other_launches);
+
+/* Number of kernels the library launched since the context was created
+ * (a graph replay counts each of its kernel nodes). */
+pt_status pt_get_launch_count(pt_ctx* ctx, int64_t* launches);
+
+/* Host-only planner, usable without a GPU: orient the edges of a join
+ * graph of n_tables tables with the given row counts (src_out/dst_out,
+ * n_edges entries), the forward visiting order (order_out, n_tables) and
+ * each table's forward level (level_out, n_tables; longest path from a
+ * source, so tables of one level are independent). */
+pt_status pt_plan_graph(int32_t n_tables, const int64_t* n_rows, int32_t n_edges, const pt_edge* edges,
+                        int32_t* src_out, int32_t* dst_out, int32_t* order_out, int32_t* level_out);
+
+/* Message of the last failed call on ctx (or of the last failed pt_create /
+ * pt_plan_graph when ctx is NULL).  Valid until the next call on ctx. */
+const char* pt_last_error(pt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

@@ -1,0 +1,82 @@
+// Internal interface between the host runtime (pt_runtime.cu) and the
+// device kernels (pt_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pt {
+
+constexpr int kMaxIn = 8;         // incoming edges of one visit
+constexpr int kMaxOut = 8;        // outgoing edges of one visit
+constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
+constexpr int kWordsPerIter = 4;  // bitmap words (32 rows each) a warp scans per iteration
+
+struct ColRef {
+    const void* p;
+    int32_t dtype;  // 0 = int32, 1 = int64
+    int32_t pad;
+};
+
+// An incoming edge of a visit: the visit's key column(s) on the edge and
+// the filter the other end built earlier in the same pass.
+struct ProbeEdge {
+    ColRef col[2];
+    int32_t ncols;
+    int32_t edge_id;
+    const uint32_t* filter;
+    const int64_t* nblocks;                   // written by the builder's size/clear kernel
+    const unsigned long long* build_count;    // survivors of the building visit
+    int64_t build_rows;                       // rows of the building table
+};
+
+// An outgoing edge: the visit's key column(s) and the filter it builds.
+struct BuildEdge {
+    ColRef col[2];
+    int32_t ncols;
+    int32_t edge_id;
+    uint32_t* filter;
+    int64_t* nblocks;
+    int64_t probe_rows;  // rows of the table at the other end (size rule)
+};
+
+struct FilterCfg {
+    int32_t bits_per_key;
+    int32_t k;
+    int32_t block_bits;
+    int32_t pad;
+    uint64_t seed;
+};
+
+// Everything one visit (table, pass) needs.  Passed by value as a kernel
+// parameter (well under the 4 KB parameter limit).
+struct VisitArgs {
+    int64_t n;                       // rows
+    const uint32_t* in_bits;         // input bitmap or nullptr (= all rows)
+    uint32_t* out_bits;              // survivor bitmap
+    uint32_t* ids;                   // compacted survivor row ids (nullptr: visit builds nothing)
+    uint32_t* seg_count;             // survivors per scan warp (segment), nullptr if ids is
+    unsigned long long* count;       // total survivors (zeroed before the pass)
+    unsigned long long* stats;       // [0] probe sectors, [1] build sectors (zeroed before the pass)
+    int32_t n_in;
+    int32_t n_out;
+    int32_t n_bcols;
+    int32_t words_per_warp;          // bitmap words per scan warp; segment s starts at row s*32*wpw
+    int32_t smem_words;              // shared-memory filter budget of one CTA (uint32 words)
+    int32_t total_warps;             // scan warps launched (= segments)
+    ProbeEdge in[kMaxIn];
+    BuildEdge out[kMaxOut];
+    ColRef bcol[kMaxBuildCols];
+};
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+
+// CTAs of the scan kernel that fit on one SM for this shape.
+int scan_max_ctas_per_sm(int block_bits, int block, size_t smem);
+cudaError_t scan_set_smem_limit(int block_bits, size_t smem);
+
+}  // namespace pt

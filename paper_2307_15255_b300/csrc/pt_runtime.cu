@@ -1,0 +1,840 @@
+// Host runtime and C ABI of libpt (declared in include/pt.h).
+//
+// The runtime keeps the registered tables and the join graph, builds the
+// transfer schedule (Section 3.2 of the paper: size-ordered edges, one
+// forward and one backward pass), lays out every buffer a run needs in one
+// device allocation, and enqueues the three kernels of each visit on the
+// context's stream.  No step of a run executes on the host: filter sizes
+// depend on survivor counts that only the device knows, so they are
+// computed by a kernel and no host synchronization happens between visits.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pt.h"
+#include "pt_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxTables = 64;
+constexpr int kMaxEdges = 64;
+constexpr int kMaxCols = 16;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Col {
+    const void* dev = nullptr;
+    int32_t dtype = 0;
+    void* owned = nullptr;  // device copy of a host column
+};
+
+struct Table {
+    int64_t n = 0;
+    std::vector<Col> cols;
+    const uint32_t* sel = nullptr;
+    void* sel_owned = nullptr;
+};
+
+// Launch shape of one visit's scan.
+struct ScanShape {
+    int grid = 1, block = 256;
+    size_t smem = 0;
+    int words_per_warp = 4, total_warps = 8;
+};
+
+struct Visit {
+    int table = 0;
+    std::vector<int> in_edges, out_edges;
+    std::vector<int> bcols;  // distinct build columns
+    int64_t max_in_filter_bytes = 0;
+    ScanShape shape;
+};
+
+}  // namespace
+
+struct pt_ctx {
+    pt::FilterCfg fcfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+
+    std::vector<Table> tables;
+    std::vector<pt_edge> edges;
+    bool graph_set = false;
+    bool planned = false;
+
+    std::vector<int32_t> src, dst, order, level;
+    std::vector<Visit> visits[2];
+
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::vector<uint32_t*> surv[2];
+    std::vector<uint32_t*> ids, seg;
+    std::vector<uint32_t*> filt[2];
+    std::vector<int64_t> filt_max_words;
+    unsigned long long* counts[2] = {nullptr, nullptr};  // [table]
+    unsigned long long* stats[2] = {nullptr, nullptr};   // [table][2]
+    int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
+    void* meta[2] = {nullptr, nullptr};
+    size_t meta_bytes = 0;
+    int64_t seg_cap = 0;
+
+    int scan_threads = 256;
+    int smem_budget = 48 * 1024;
+    int ctas_per_sm = 0;
+    int smem_attr_set[2] = {0, 0};
+    bool shapes_ready = false;
+
+    int passes_done = 0;  // bit 0: forward, bit 1: backward
+
+    bool graph_mode = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_kernels = 0;
+
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+pt_status fail(pt_ctx* ctx, pt_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_err = buf;
+    return st;
+}
+
+#define PT_CUDA(ctx, call)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail((ctx), PT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool rank_less(const std::vector<int64_t>& n, int a, int b) {
+    if (n[a] != n[b]) return n[a] < n[b];
+    return a < b;
+}
+
+pt_status check_edges(pt_ctx* ctx, int32_t n_tables, const std::vector<int>& n_cols,
+                      const std::vector<std::vector<int32_t>>* dtypes, int32_t n_edges, const pt_edge* e) {
+    if (n_edges < 0 || n_edges > kMaxEdges) return fail(ctx, PT_ERR_INVALID, "n_edges %d out of range", n_edges);
+    if (n_edges > 0 && !e) return fail(ctx, PT_ERR_INVALID, "edges is NULL");
+    for (int i = 0; i < n_edges; ++i) {
+        const pt_edge& x = e[i];
+        if (x.flags != 0) return fail(ctx, PT_ERR_UNSUPPORTED, "edge %d: flags 0x%x (one-direction edges) not implemented", i, x.flags);
+        if (x.ncols < 1 || x.ncols > 2) return fail(ctx, PT_ERR_INVALID, "edge %d: ncols %d", i, x.ncols);
+        if (x.t0 < 0 || x.t0 >= n_tables || x.t1 < 0 || x.t1 >= n_tables)
+            return fail(ctx, PT_ERR_INVALID, "edge %d: table id out of range", i);
+        if (x.t0 == x.t1) return fail(ctx, PT_ERR_INVALID, "edge %d joins table %d with itself", i, x.t0);
+        for (int j = 0; j < x.ncols; ++j) {
+            if (x.c0[j] < 0 || x.c0[j] >= n_cols[x.t0] || x.c1[j] < 0 || x.c1[j] >= n_cols[x.t1])
+                return fail(ctx, PT_ERR_INVALID, "edge %d: column index out of range", i);
+        }
+        (void)dtypes;
+    }
+    return PT_OK;
+}
+
+// Orientation, visiting order and levels (Section 3.2).
+void plan_graph(const std::vector<int64_t>& n, const std::vector<pt_edge>& e, std::vector<int32_t>& src,
+                std::vector<int32_t>& dst, std::vector<int32_t>& order, std::vector<int32_t>& level) {
+    const int T = (int)n.size(), E = (int)e.size();
+    src.assign(E, 0);
+    dst.assign(E, 0);
+    for (int i = 0; i < E; ++i) {
+        if (rank_less(n, e[i].t0, e[i].t1)) {
+            src[i] = e[i].t0;
+            dst[i] = e[i].t1;
+        } else {
+            src[i] = e[i].t1;
+            dst[i] = e[i].t0;
+        }
+    }
+    order.resize(T);
+    for (int i = 0; i < T; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rank_less(n, a, b); });
+    level.assign(T, 0);
+    for (int v : order)  // ascending rank is a topological order: every edge goes up in rank
+        for (int i = 0; i < E; ++i)
+            if (src[i] == v) level[dst[i]] = std::max(level[dst[i]], level[v] + 1);
+}
+
+int64_t max_filter_words(int64_t n0, int64_t n1, const pt::FilterCfg& f) {
+    const int64_t m = std::min(n0, n1);
+    int64_t nb = (m * f.bits_per_key + f.block_bits - 1) / f.block_bits;
+    if (nb < 1) nb = 1;
+    return nb * (f.block_bits / 32);
+}
+
+void free_arena(pt_ctx* ctx) {
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    if (ctx->arena) {
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+    }
+    ctx->arena_bytes = 0;
+}
+
+pt_status upload_table(pt_ctx* ctx, Table& t, int32_t n_cols, const pt_column* cols, const uint32_t* sel,
+                       int32_t sel_mem, bool fresh) {
+    for (int j = 0; j < n_cols; ++j) {
+        const pt_column& c = cols[j];
+        Col& d = t.cols[j];
+        const size_t bytes = (size_t)t.n * (c.dtype == PT_I32 ? 4 : 8);
+        if (c.mem == PT_MEM_HOST) {
+            if (!d.owned && bytes > 0) {
+                if (cudaMalloc(&d.owned, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    d.owned = nullptr;
+                    return fail(ctx, PT_ERR_OOM, "device copy of a host column (%zu bytes)", bytes);
+                }
+            }
+            if (bytes) PT_CUDA(ctx, cudaMemcpyAsync(d.owned, c.data, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            d.dev = d.owned;
+        } else {
+            d.dev = c.data;
+        }
+        d.dtype = c.dtype;
+    }
+    (void)fresh;
+    const size_t sbytes = (size_t)((t.n + 31) / 32) * 4;
+    if (sel && sel_mem == PT_MEM_HOST) {
+        if (!t.sel_owned && sbytes) {
+            if (cudaMalloc(&t.sel_owned, sbytes) != cudaSuccess) {
+                cudaGetLastError();
+                t.sel_owned = nullptr;
+                return fail(ctx, PT_ERR_OOM, "device copy of a host selection bitmap");
+            }
+        }
+        if (sbytes) PT_CUDA(ctx, cudaMemcpyAsync(t.sel_owned, sel, sbytes, cudaMemcpyHostToDevice, ctx->stream));
+        t.sel = (const uint32_t*)t.sel_owned;
+    } else {
+        t.sel = sel;
+    }
+    return PT_OK;
+}
+
+pt_status check_columns(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_column* cols, int32_t sel_mem) {
+    if (n_cols < 1 || n_cols > kMaxCols) return fail(ctx, PT_ERR_INVALID, "n_cols %d out of range", n_cols);
+    if (!cols) return fail(ctx, PT_ERR_INVALID, "cols is NULL");
+    for (int j = 0; j < n_cols; ++j) {
+        if (cols[j].dtype != PT_I32 && cols[j].dtype != PT_I64) return fail(ctx, PT_ERR_INVALID, "column %d: dtype %d", j, cols[j].dtype);
+        if (cols[j].mem != PT_MEM_DEVICE && cols[j].mem != PT_MEM_HOST) return fail(ctx, PT_ERR_INVALID, "column %d: mem %d", j, cols[j].mem);
+        if (n_rows > 0 && !cols[j].data) return fail(ctx, PT_ERR_INVALID, "column %d: data is NULL", j);
+        if (cols[j].mem == PT_MEM_DEVICE && ((uintptr_t)cols[j].data % 16) != 0)
+            return fail(ctx, PT_ERR_INVALID, "column %d: device data must be 16-byte aligned", j);
+    }
+    if (sel_mem != PT_MEM_DEVICE && sel_mem != PT_MEM_HOST) return fail(ctx, PT_ERR_INVALID, "sel_mem %d", sel_mem);
+    return PT_OK;
+}
+
+ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
+    ScanShape s{};
+    const int64_t n = ctx->tables[vis.table].n;
+    const int64_t n_words = (n + 31) / 32;
+    s.block = ctx->scan_threads;
+    const int64_t want_smem = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
+    s.smem = (size_t)((want_smem + 15) / 16 * 16);
+    int fit = pt::scan_max_ctas_per_sm(ctx->fcfg.block_bits, s.block, s.smem);
+    if (fit < 1) fit = 1;
+    if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
+    const int warps_per_cta = s.block / 32;
+    const int64_t max_grid = (int64_t)ctx->num_sms * fit;
+    const int64_t want_warps = (n_words + pt::kWordsPerIter - 1) / pt::kWordsPerIter;
+    int64_t grid = (want_warps + warps_per_cta - 1) / warps_per_cta;
+    grid = std::max<int64_t>(1, std::min(grid, max_grid));
+    s.grid = (int)grid;
+    s.total_warps = (int)(grid * warps_per_cta);
+    int64_t wpw = (n_words + s.total_warps - 1) / s.total_warps;
+    wpw = (wpw + pt::kWordsPerIter - 1) / pt::kWordsPerIter * pt::kWordsPerIter;
+    if (wpw < pt::kWordsPerIter) wpw = pt::kWordsPerIter;
+    s.words_per_warp = (int)wpw;
+    return s;
+}
+
+pt::ColRef colref(const pt_ctx* ctx, int t, int c) {
+    pt::ColRef r{};
+    r.p = ctx->tables[t].cols[c].dev;
+    r.dtype = ctx->tables[t].cols[c].dtype;
+    return r;
+}
+
+void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, pt::VisitArgs& a) {
+    std::memset(&a, 0, sizeof a);
+    const int v = vis.table;
+    a.n = ctx->tables[v].n;
+    a.in_bits = p == 0 ? ctx->tables[v].sel : ctx->surv[0][v];
+    a.out_bits = ctx->surv[p][v];
+    a.count = ctx->counts[p] + v;
+    a.stats = ctx->stats[p] + 2 * v;
+    a.n_in = (int)vis.in_edges.size();
+    a.n_out = (int)vis.out_edges.size();
+    a.words_per_warp = sh.words_per_warp;
+    a.total_warps = sh.total_warps;
+    a.smem_words = (int32_t)(sh.smem / 4);
+    for (int i = 0; i < a.n_in; ++i) {
+        const int e = vis.in_edges[i];
+        const pt_edge& ed = ctx->edges[e];
+        const int32_t* cs = ed.t0 == v ? ed.c0 : ed.c1;
+        const int b = p == 0 ? ctx->src[e] : ctx->dst[e];  // the table that built the filter
+        pt::ProbeEdge& pe = a.in[i];
+        pe.ncols = ed.ncols;
+        pe.edge_id = e;
+        pe.col[0] = colref(ctx, v, cs[0]);
+        pe.col[1] = ed.ncols == 2 ? colref(ctx, v, cs[1]) : pe.col[0];
+        pe.filter = ctx->filt[p][e];
+        pe.nblocks = ctx->nblocks[p] + e;
+        pe.build_count = ctx->counts[p] + b;
+        pe.build_rows = ctx->tables[b].n;
+    }
+    for (int i = 0; i < a.n_out; ++i) {
+        const int e = vis.out_edges[i];
+        const pt_edge& ed = ctx->edges[e];
+        const int32_t* cs = ed.t0 == v ? ed.c0 : ed.c1;
+        const int other = ed.t0 == v ? ed.t1 : ed.t0;
+        pt::BuildEdge& be = a.out[i];
+        be.ncols = ed.ncols;
+        be.edge_id = e;
+        be.col[0] = colref(ctx, v, cs[0]);
+        be.col[1] = ed.ncols == 2 ? colref(ctx, v, cs[1]) : be.col[0];
+        be.filter = ctx->filt[p][e];
+        be.nblocks = ctx->nblocks[p] + e;
+        be.probe_rows = ctx->tables[other].n;
+    }
+    a.n_bcols = (int)vis.bcols.size();
+    for (int i = 0; i < a.n_bcols; ++i) a.bcol[i] = colref(ctx, v, vis.bcols[i]);
+    if (a.n_out > 0) {
+        a.ids = ctx->ids[v];
+        a.seg_count = ctx->seg[v];
+    }
+}
+
+// Compute every visit's scan shape and raise the kernels' dynamic shared
+// memory limit; done before any capture (occupancy queries and function
+// attributes are not stream work).
+pt_status prepare_shapes(pt_ctx* ctx) {
+    if (ctx->shapes_ready) return PT_OK;
+    size_t max_smem = 0;
+    for (int p = 0; p < 2; ++p)
+        for (Visit& vis : ctx->visits[p]) max_smem = std::max(max_smem, (size_t)((std::min<int64_t>(
+            ctx->smem_budget, vis.in_edges.empty() ? 0 : vis.max_in_filter_bytes) + 15) / 16 * 16));
+    const int bi = ctx->fcfg.block_bits == 512 ? 1 : 0;
+    if ((int)max_smem > ctx->smem_attr_set[bi]) {
+        PT_CUDA(ctx, pt::scan_set_smem_limit(ctx->fcfg.block_bits, max_smem));
+        ctx->smem_attr_set[bi] = (int)max_smem;
+    }
+    for (int p = 0; p < 2; ++p)
+        for (Visit& vis : ctx->visits[p]) vis.shape = scan_shape(ctx, vis);
+    ctx->shapes_ready = true;
+    return PT_OK;
+}
+
+pt_status record_event(pt_ctx* ctx, int kind) {
+    if (!ctx->timing) return PT_OK;
+    if (ctx->ev_used == ctx->ev.size()) {
+        cudaEvent_t e;
+        PT_CUDA(ctx, cudaEventCreate(&e));
+        ctx->ev.push_back(e);
+        ctx->ev_kind.push_back(0);
+    }
+    ctx->ev_kind[ctx->ev_used] = kind;
+    PT_CUDA(ctx, cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+    ctx->ev_used++;
+    return PT_OK;
+}
+
+pt_status enqueue_pass(pt_ctx* ctx, int p) {
+    if (!ctx->shapes_ready) return fail(ctx, PT_ERR_STATE, "launch shapes not prepared");
+    PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
+    for (const Visit& vis : ctx->visits[p]) {
+        const ScanShape& sh = vis.shape;
+        pt::VisitArgs a;
+        fill_visit_args(ctx, p, vis, sh, a);
+        pt_status st;
+        if ((st = record_event(ctx, 0)) != PT_OK) return st;
+        PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, ctx->stream));
+        if ((st = record_event(ctx, 0)) != PT_OK) return st;
+        ctx->launches++;
+        if (a.n_out > 0) {
+            int64_t words = 0;
+            for (int e : vis.out_edges) words = std::max(words, ctx->filt_max_words[e]);
+            const int64_t n16 = words / 4;
+            int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
+            if ((st = record_event(ctx, 1)) != PT_OK) return st;
+            PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, ctx->stream));
+            const int grid_i = std::max(1, std::min(sh.total_warps / 16 + 1, ctx->num_sms * 4));
+            PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, ctx->stream));
+            if ((st = record_event(ctx, 1)) != PT_OK) return st;
+            ctx->launches += 2;
+        }
+    }
+    return PT_OK;
+}
+
+pt_status require_plan(pt_ctx* ctx) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (!ctx->planned) return fail(ctx, PT_ERR_STATE, "pt_plan has not run");
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t pt_abi_version(void) { return (1u << 16) | 0u; }
+
+pt_status pt_create(pt_ctx** out, const pt_filter_cfg* cfg, void* cuda_stream) {
+    if (!out || !cfg) return fail(nullptr, PT_ERR_INVALID, "out or cfg is NULL");
+    *out = nullptr;
+    if (cfg->block_bits != 256 && cfg->block_bits != 512)
+        return fail(nullptr, PT_ERR_INVALID, "block_bits must be 256 or 512 (got %d)", cfg->block_bits);
+    if (cfg->k < 1 || cfg->k > 16) return fail(nullptr, PT_ERR_INVALID, "k must be in 1..16 (got %d)", cfg->k);
+    if (cfg->bits_per_key < 1 || cfg->bits_per_key > 64)
+        return fail(nullptr, PT_ERR_INVALID, "bits_per_key must be in 1..64 (got %d)", cfg->bits_per_key);
+    if (cfg->reserved != 0) return fail(nullptr, PT_ERR_INVALID, "reserved must be 0");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, PT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, PT_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    pt_ctx* ctx = new (std::nothrow) pt_ctx();
+    if (!ctx) return fail(nullptr, PT_ERR_OOM, "host allocation");
+    ctx->fcfg.bits_per_key = cfg->bits_per_key;
+    ctx->fcfg.k = cfg->k;
+    ctx->fcfg.block_bits = cfg->block_bits;
+    ctx->fcfg.seed = cfg->seed;
+    ctx->device = dev;
+    ctx->num_sms = sms;
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, PT_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return PT_OK;
+}
+
+pt_status pt_destroy(pt_ctx* ctx) {
+    if (!ctx) return PT_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_arena(ctx);
+    for (Table& t : ctx->tables) {
+        for (Col& c : t.cols)
+            if (c.owned) cudaFree(c.owned);
+        if (t.sel_owned) cudaFree(t.sel_owned);
+    }
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return PT_OK;
+}
+
+pt_status pt_register_table(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_column* cols,
+                            const uint32_t* sel, int32_t sel_mem, int32_t* table_id) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (ctx->planned || ctx->graph_set) return fail(ctx, PT_ERR_STATE, "tables are registered before the join graph and the plan");
+    if (n_rows < 0 || n_rows > 0x7FFFFFFFll) return fail(ctx, PT_ERR_INVALID, "n_rows %lld out of range", (long long)n_rows);
+    if ((int)ctx->tables.size() >= kMaxTables) return fail(ctx, PT_ERR_INVALID, "more than %d tables", kMaxTables);
+    pt_status st = check_columns(ctx, n_rows, n_cols, cols, sel_mem);
+    if (st != PT_OK) return st;
+    if (sel && sel_mem == PT_MEM_DEVICE && ((uintptr_t)sel % 16) != 0)
+        return fail(ctx, PT_ERR_INVALID, "device selection bitmap must be 16-byte aligned");
+    Table t;
+    t.n = n_rows;
+    t.cols.resize(n_cols);
+    st = upload_table(ctx, t, n_cols, cols, sel, sel_mem, true);
+    if (st != PT_OK) {
+        for (Col& c : t.cols)
+            if (c.owned) cudaFree(c.owned);
+        if (t.sel_owned) cudaFree(t.sel_owned);
+        return st;
+    }
+    ctx->tables.push_back(t);
+    if (table_id) *table_id = (int32_t)ctx->tables.size() - 1;
+    return PT_OK;
+}
+
+pt_status pt_update_table(pt_ctx* ctx, int32_t table_id, const pt_column* cols, const uint32_t* sel,
+                          int32_t sel_mem) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
+    Table& t = ctx->tables[table_id];
+    pt_status st = check_columns(ctx, t.n, (int32_t)t.cols.size(), cols, sel_mem);
+    if (st != PT_OK) return st;
+    for (size_t j = 0; j < t.cols.size(); ++j)
+        if (cols[j].dtype != t.cols[j].dtype) return fail(ctx, PT_ERR_INVALID, "column %zu changes dtype", j);
+    if (sel && sel_mem == PT_MEM_DEVICE && ((uintptr_t)sel % 16) != 0)
+        return fail(ctx, PT_ERR_INVALID, "device selection bitmap must be 16-byte aligned");
+    if (ctx->planned && ((sel == nullptr) != (t.sel == nullptr)))
+        return fail(ctx, PT_ERR_INVALID, "a planned table keeps having (or not having) a selection bitmap");
+    st = upload_table(ctx, t, (int32_t)t.cols.size(), cols, sel, sel_mem, false);
+    if (st != PT_OK) return st;
+    if (ctx->gexec) {  // captured kernel parameters hold the old pointers
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->passes_done = 0;
+    return PT_OK;
+}
+
+pt_status pt_set_join_graph(pt_ctx* ctx, int32_t n_edges, const pt_edge* edges) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (ctx->planned) return fail(ctx, PT_ERR_STATE, "the join graph is fixed once planned");
+    std::vector<int> ncols;
+    for (const Table& t : ctx->tables) ncols.push_back((int)t.cols.size());
+    pt_status st = check_edges(ctx, (int32_t)ctx->tables.size(), ncols, nullptr, n_edges, edges);
+    if (st != PT_OK) return st;
+    ctx->edges.assign(edges, edges + n_edges);
+    ctx->graph_set = true;
+    return PT_OK;
+}
+
+pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (ctx->planned) return fail(ctx, PT_ERR_STATE, "already planned");
+    const int T = (int)ctx->tables.size(), E = (int)ctx->edges.size();
+    if (T == 0) return fail(ctx, PT_ERR_STATE, "no tables registered");
+    std::vector<int64_t> n(T);
+    for (int v = 0; v < T; ++v) n[v] = ctx->tables[v].n;
+    plan_graph(n, ctx->edges, ctx->src, ctx->dst, ctx->order, ctx->level);
+
+    const pt::FilterCfg& f = ctx->fcfg;
+    ctx->filt_max_words.assign(E, 0);
+    for (int e = 0; e < E; ++e)
+        ctx->filt_max_words[e] = max_filter_words(n[ctx->edges[e].t0], n[ctx->edges[e].t1], f);
+
+    for (int p = 0; p < 2; ++p) {
+        ctx->visits[p].clear();
+        for (int oi = 0; oi < T; ++oi) {
+            Visit vis;
+            vis.table = p == 0 ? ctx->order[oi] : ctx->order[T - 1 - oi];
+            for (int e = 0; e < E; ++e) {
+                const int into = p == 0 ? ctx->dst[e] : ctx->src[e];
+                const int from = p == 0 ? ctx->src[e] : ctx->dst[e];
+                if (into == vis.table) {
+                    vis.in_edges.push_back(e);
+                    vis.max_in_filter_bytes += ctx->filt_max_words[e] * 4;
+                }
+                if (from == vis.table) {
+                    vis.out_edges.push_back(e);
+                    const pt_edge& ed = ctx->edges[e];
+                    const int32_t* cs = ed.t0 == vis.table ? ed.c0 : ed.c1;
+                    for (int j = 0; j < ed.ncols; ++j)
+                        if (std::find(vis.bcols.begin(), vis.bcols.end(), cs[j]) == vis.bcols.end()) vis.bcols.push_back(cs[j]);
+                }
+            }
+            if ((int)vis.in_edges.size() > pt::kMaxIn || (int)vis.out_edges.size() > pt::kMaxOut ||
+                (int)vis.bcols.size() > pt::kMaxBuildCols)
+                return fail(ctx, PT_ERR_UNSUPPORTED, "table %d has more than %d incoming or %d outgoing edges in a pass",
+                            vis.table, pt::kMaxIn, pt::kMaxOut);
+            ctx->visits[p].push_back(vis);
+        }
+    }
+
+    // one device allocation holds every buffer of a run
+    ctx->seg_cap = (int64_t)ctx->num_sms * 64;  // at most 64 resident warps per SM
+    std::vector<bool> has_edge(T, false);
+    for (int e = 0; e < E; ++e) has_edge[ctx->edges[e].t0] = has_edge[ctx->edges[e].t1] = true;
+    size_t off = 0;
+    std::vector<size_t> o_surv[2], o_ids(T), o_seg(T), o_filt[2];
+    for (int p = 0; p < 2; ++p) {
+        o_surv[p].resize(T);
+        o_filt[p].resize(E);
+    }
+    for (int v = 0; v < T; ++v) {
+        const size_t wb = (size_t)((n[v] + 31) / 32) * 4;
+        for (int p = 0; p < 2; ++p) {
+            o_surv[p][v] = off;
+            off += align_up(std::max<size_t>(wb, 16));
+        }
+        o_ids[v] = off;
+        if (has_edge[v]) off += align_up(std::max<size_t>((size_t)n[v] * 4, 16));
+        o_seg[v] = off;
+        if (has_edge[v]) off += align_up((size_t)ctx->seg_cap * 4);
+    }
+    for (int e = 0; e < E; ++e)
+        for (int p = 0; p < 2; ++p) {
+            o_filt[p][e] = off;
+            off += align_up((size_t)ctx->filt_max_words[e] * 4);
+        }
+    ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 16 + (size_t)std::max(E, 1) * 8);
+    size_t o_meta[2];
+    for (int p = 0; p < 2; ++p) {
+        o_meta[p] = off;
+        off += ctx->meta_bytes;
+    }
+    void* arena = nullptr;
+    if (cudaMalloc(&arena, off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PT_ERR_OOM, "device arena of %zu bytes", off);
+    }
+    ctx->arena = arena;
+    ctx->arena_bytes = off;
+    char* base = (char*)arena;
+    for (int p = 0; p < 2; ++p) {
+        ctx->surv[p].resize(T);
+        ctx->filt[p].resize(E);
+        for (int v = 0; v < T; ++v) ctx->surv[p][v] = (uint32_t*)(base + o_surv[p][v]);
+        for (int e = 0; e < E; ++e) ctx->filt[p][e] = (uint32_t*)(base + o_filt[p][e]);
+        ctx->meta[p] = base + o_meta[p];
+        ctx->counts[p] = (unsigned long long*)(base + o_meta[p]);
+        ctx->stats[p] = (unsigned long long*)(base + o_meta[p] + (size_t)T * 8);
+        ctx->nblocks[p] = (int64_t*)(base + o_meta[p] + (size_t)T * 24);
+    }
+    ctx->ids.resize(T);
+    ctx->seg.resize(T);
+    for (int v = 0; v < T; ++v) {
+        ctx->ids[v] = has_edge[v] ? (uint32_t*)(base + o_ids[v]) : nullptr;
+        ctx->seg[v] = has_edge[v] ? (uint32_t*)(base + o_seg[v]) : nullptr;
+    }
+    // bitmaps of tables nobody visits with data still read as zero tails
+    PT_CUDA(ctx, cudaMemsetAsync(arena, 0, off, ctx->stream));
+    ctx->planned = true;
+    ctx->passes_done = 0;
+    if (order_out)
+        for (int i = 0; i < T; ++i) order_out[i] = ctx->order[i];
+    if (mem_bytes_out) *mem_bytes_out = (int64_t)off;
+    return PT_OK;
+}
+
+pt_status pt_run_forward(pt_ctx* ctx) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if ((st = prepare_shapes(ctx)) != PT_OK) return st;
+    st = enqueue_pass(ctx, 0);
+    if (st != PT_OK) return st;
+    ctx->passes_done = 1;
+    return PT_OK;
+}
+
+pt_status pt_run_backward(pt_ctx* ctx) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (!(ctx->passes_done & 1)) return fail(ctx, PT_ERR_STATE, "the backward pass needs a forward pass first");
+    if ((st = prepare_shapes(ctx)) != PT_OK) return st;
+    st = enqueue_pass(ctx, 1);
+    if (st != PT_OK) return st;
+    ctx->passes_done |= 2;
+    return PT_OK;
+}
+
+pt_status pt_run_transfer(pt_ctx* ctx) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (!ctx->graph_mode) {
+        st = pt_run_forward(ctx);
+        if (st != PT_OK) return st;
+        return pt_run_backward(ctx);
+    }
+    if ((st = prepare_shapes(ctx)) != PT_OK) return st;
+    if (!ctx->gexec) {
+        const bool timing = ctx->timing;
+        ctx->timing = false;  // no event records inside the captured graph
+        const int64_t before = ctx->launches;
+        PT_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        pt_status s0 = enqueue_pass(ctx, 0);
+        pt_status s1 = s0 == PT_OK ? enqueue_pass(ctx, 1) : s0;
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        ctx->timing = timing;
+        ctx->graph_kernels = ctx->launches - before;
+        ctx->launches = before;
+        if (s1 != PT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s1;
+        }
+        if (ce != cudaSuccess) return fail(ctx, PT_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return fail(ctx, PT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
+        }
+    }
+    if ((st = record_event(ctx, 2)) != PT_OK) return st;
+    PT_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+    if ((st = record_event(ctx, 2)) != PT_OK) return st;
+    ctx->launches += ctx->graph_kernels;
+    ctx->passes_done = 3;
+    return PT_OK;
+}
+
+pt_status pt_set_graph_mode(pt_ctx* ctx, int32_t on) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    ctx->graph_mode = on != 0;
+    if (!ctx->graph_mode && ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return PT_OK;
+}
+
+pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uint32_t* bitmap_out,
+                                int64_t* count_out) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (pass < 0 || pass > 1) return fail(ctx, PT_ERR_INVALID, "pass %d", pass);
+    if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
+    if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
+    const size_t bytes = (size_t)((ctx->tables[table_id].n + 31) / 32) * 4;
+    if (bitmap_out && bytes)
+        PT_CUDA(ctx, cudaMemcpyAsync(bitmap_out, ctx->surv[pass][table_id], bytes, cudaMemcpyDefault, ctx->stream));
+    unsigned long long c = 0;
+    if (count_out)
+        PT_CUDA(ctx, cudaMemcpyAsync(&c, ctx->counts[pass] + table_id, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (count_out) *count_out = (int64_t)c;
+    return PT_OK;
+}
+
+pt_status pt_get_survivors(pt_ctx* ctx, int32_t table_id, uint32_t* bitmap_out, int64_t* count_out) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    return pt_get_pass_survivors(ctx, (ctx->passes_done & 2) ? 1 : 0, table_id, bitmap_out, count_out);
+}
+
+pt_status pt_get_filter(pt_ctx* ctx, int32_t pass, int32_t edge_id, uint32_t* words_out, int64_t* nblocks_out) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (pass < 0 || pass > 1) return fail(ctx, PT_ERR_INVALID, "pass %d", pass);
+    if (edge_id < 0 || edge_id >= (int)ctx->edges.size()) return fail(ctx, PT_ERR_INVALID, "edge id %d", edge_id);
+    if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
+    int64_t nb = 0;
+    PT_CUDA(ctx, cudaMemcpyAsync(&nb, ctx->nblocks[pass] + edge_id, sizeof nb, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (words_out && nb > 0)
+        PT_CUDA(ctx, cudaMemcpyAsync(words_out, ctx->filt[pass][edge_id], (size_t)nb * ctx->fcfg.block_bits / 8,
+                                     cudaMemcpyDefault, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (nblocks_out) *nblocks_out = nb;
+    return PT_OK;
+}
+
+pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_visit_stats* out) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (pass < 0 || pass > 1 || !out) return fail(ctx, PT_ERR_INVALID, "pass %d / out NULL", pass);
+    if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
+    if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
+    const int T = (int)ctx->tables.size(), E = (int)ctx->edges.size();
+    std::vector<unsigned long long> c(T), s(2 * T);
+    std::vector<int64_t> nb(std::max(E, 1));
+    PT_CUDA(ctx, cudaMemcpyAsync(c.data(), ctx->counts[pass], T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaMemcpyAsync(s.data(), ctx->stats[pass], 2 * T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (E) PT_CUDA(ctx, cudaMemcpyAsync(nb.data(), ctx->nblocks[pass], E * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const Visit* vis = nullptr;
+    for (const Visit& x : ctx->visits[pass])
+        if (x.table == table_id) vis = &x;
+    std::memset(out, 0, sizeof *out);
+    out->n_rows = ctx->tables[table_id].n;
+    out->survivors = (int64_t)c[table_id];
+    out->probe_sectors = (int64_t)s[2 * table_id];
+    out->build_sectors = (int64_t)s[2 * table_id + 1];
+    out->n_in = (int32_t)vis->in_edges.size();
+    out->n_out = (int32_t)vis->out_edges.size();
+    for (int e : vis->out_edges) out->filter_bytes += nb[e] * ctx->fcfg.block_bits / 8;
+    out->has_input_bitmap = pass == 1 || ctx->tables[table_id].sel != nullptr;
+    return PT_OK;
+}
+
+pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (threads < 128 || threads > 1024 || threads % 32) return fail(ctx, PT_ERR_INVALID, "threads %d", threads);
+    if (smem_filter_bytes < 0 || smem_filter_bytes > 220 * 1024) return fail(ctx, PT_ERR_INVALID, "smem %d", smem_filter_bytes);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(ctx, PT_ERR_INVALID, "ctas_per_sm %d", ctas_per_sm);
+    ctx->scan_threads = threads;
+    ctx->smem_budget = smem_filter_bytes / 16 * 16;
+    ctx->ctas_per_sm = ctas_per_sm;
+    ctx->shapes_ready = false;
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return PT_OK;
+}
+
+pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    ctx->timing = on != 0;
+    ctx->ev_used = 0;
+    return PT_OK;
+}
+
+pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
+                             int32_t* other_launches) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double t[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float ms = 0.f;
+        PT_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        const int k = ctx->ev_kind[i];
+        t[k] += ms;
+        n[k] += 1;
+    }
+    if (scan_ms) *scan_ms = t[0];
+    if (scan_launches) *scan_launches = n[0];
+    if (other_ms) *other_ms = t[1] + t[2];
+    if (other_launches) *other_launches = n[1] + n[2];
+    return PT_OK;
+}
+
+pt_status pt_get_launch_count(pt_ctx* ctx, int64_t* launches) {
+    if (!ctx || !launches) return fail(ctx, PT_ERR_INVALID, "ctx or launches is NULL");
+    *launches = ctx->launches;
+    return PT_OK;
+}
+
+pt_status pt_plan_graph(int32_t n_tables, const int64_t* n_rows, int32_t n_edges, const pt_edge* edges,
+                        int32_t* src_out, int32_t* dst_out, int32_t* order_out, int32_t* level_out) {
+    if (n_tables < 1 || n_tables > kMaxTables || !n_rows) return fail(nullptr, PT_ERR_INVALID, "n_tables %d", n_tables);
+    std::vector<int> ncols(n_tables, kMaxCols);  // column indexes are not known here
+    pt_status st = check_edges(nullptr, n_tables, ncols, nullptr, n_edges, edges);
+    if (st != PT_OK) return st;
+    std::vector<int64_t> n(n_rows, n_rows + n_tables);
+    std::vector<pt_edge> e(edges, edges + n_edges);
+    std::vector<int32_t> src, dst, order, level;
+    plan_graph(n, e, src, dst, order, level);
+    for (int i = 0; i < n_edges; ++i) {
+        if (src_out) src_out[i] = src[i];
+        if (dst_out) dst_out[i] = dst[i];
+    }
+    for (int i = 0; i < n_tables; ++i) {
+        if (order_out) order_out[i] = order[i];
+        if (level_out) level_out[i] = level[i];
+    }
+    return PT_OK;
+}
+
+const char* pt_last_error(pt_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+"""ctypes binding of libpt.so with the C ABI's names (include/pt.h).
+
+Argument marshalling only: every step of a transfer runs in the library's
+CUDA kernels.  Pointers are passed as Python ints (``tensor.data_ptr()``
+or ``ndarray.ctypes.data``).  Each call raises :class:`PtError` when the
+library returns a status other than ``PT_OK``.  If ``libpt.so`` has not
+been built, importing this module raises ``ImportError``: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence, Tuple
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpt.so")
+
+PT_OK, PT_ERR_INVALID, PT_ERR_OOM, PT_ERR_CUDA, PT_ERR_STATE, PT_ERR_TIMEOUT, PT_ERR_UNSUPPORTED = range(7)
+PT_I32, PT_I64 = 0, 1
+PT_MEM_DEVICE, PT_MEM_HOST = 0, 1
+STATUS_NAMES = ["PT_OK", "PT_ERR_INVALID", "PT_ERR_OOM", "PT_ERR_CUDA", "PT_ERR_STATE", "PT_ERR_TIMEOUT",
+                "PT_ERR_UNSUPPORTED"]
+
+
+class PtError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{func}: {name}: {msg}")
+
+
+class pt_filter_cfg(C.Structure):
+    _fields_ = [("bits_per_key", C.c_int32), ("k", C.c_int32), ("block_bits", C.c_int32),
+                ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
+class pt_column(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("mem", C.c_int32)]
+
+
+class pt_edge(C.Structure):
+    _fields_ = [("t0", C.c_int32), ("ncols", C.c_int32), ("c0", C.c_int32 * 2), ("t1", C.c_int32),
+                ("c1", C.c_int32 * 2), ("flags", C.c_uint32)]
+
+
+class pt_visit_stats(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("survivors", C.c_int64), ("probe_sectors", C.c_int64),
+                ("build_sectors", C.c_int64), ("filter_bytes", C.c_int64), ("n_in", C.c_int32),
+                ("n_out", C.c_int32), ("has_input_bitmap", C.c_int32), ("reserved", C.c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built (python -m paper_2307_15255_b300.build); "
+                      "there is no non-CUDA fallback")
+
+lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_SIGS = {
+    "pt_abi_version": (C.c_uint32, []),
+    "pt_create": (C.c_int, [C.POINTER(_P), C.POINTER(pt_filter_cfg), _P]),
+    "pt_destroy": (C.c_int, [_P]),
+    "pt_register_table": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(pt_column), _P, C.c_int32,
+                                    C.POINTER(C.c_int32)]),
+    "pt_update_table": (C.c_int, [_P, C.c_int32, C.POINTER(pt_column), _P, C.c_int32]),
+    "pt_set_join_graph": (C.c_int, [_P, C.c_int32, C.POINTER(pt_edge)]),
+    "pt_plan": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
+    "pt_run_forward": (C.c_int, [_P]),
+    "pt_run_backward": (C.c_int, [_P]),
+    "pt_run_transfer": (C.c_int, [_P]),
+    "pt_set_graph_mode": (C.c_int, [_P, C.c_int32]),
+    "pt_get_survivors": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_int64)]),
+    "pt_get_pass_survivors": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_int64)]),
+    "pt_get_filter": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_int64)]),
+    "pt_get_visit_stats": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(pt_visit_stats)]),
+    "pt_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "pt_set_kernel_timing": (C.c_int, [_P, C.c_int32]),
+    "pt_get_kernel_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "pt_get_launch_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "pt_plan_graph": (C.c_int, [C.c_int32, _P, C.c_int32, C.POINTER(pt_edge), _P, _P, _P, _P]),
+    "pt_last_error": (C.c_char_p, [_P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def pt_last_error(ctx: Optional[int] = None) -> str:
+    return lib.pt_last_error(ctx).decode(errors="replace")
+
+
+def _check(status: int, func: str, ctx: Optional[int]) -> None:
+    if status != PT_OK:
+        raise PtError(status, func, pt_last_error(ctx))
+
+
+def pt_abi_version() -> int:
+    return int(lib.pt_abi_version())
+
+
+def pt_create(bits_per_key: int = 10, k: int = 4, block_bits: int = 256, seed: int = 0,
+              stream: Optional[int] = None) -> int:
+    cfg = pt_filter_cfg(bits_per_key, k, block_bits, 0, seed)
+    out = _P()
+    _check(lib.pt_create(C.byref(out), C.byref(cfg), stream), "pt_create", None)
+    return out.value
+
+
+def pt_destroy(ctx: int) -> None:
+    _check(lib.pt_destroy(ctx), "pt_destroy", None)
+
+
+def _columns(cols: Sequence[Tuple[int, int, int]]):
+    arr = (pt_column * len(cols))()
+    for i, (ptr, dtype, mem) in enumerate(cols):
+        arr[i].data = ptr
+        arr[i].dtype = dtype
+        arr[i].mem = mem
+    return arr
+
+
+def pt_register_table(ctx: int, n_rows: int, cols: Sequence[Tuple[int, int, int]],
+                      sel: Optional[int] = None, sel_mem: int = PT_MEM_DEVICE) -> int:
+    """cols: (pointer, PT_I32/PT_I64, PT_MEM_DEVICE/PT_MEM_HOST) per key column."""
+    arr = _columns(cols)
+    tid = C.c_int32()
+    _check(lib.pt_register_table(ctx, n_rows, len(cols), arr, sel, sel_mem, C.byref(tid)),
+           "pt_register_table", ctx)
+    return tid.value
+
+
+def pt_update_table(ctx: int, table_id: int, cols: Sequence[Tuple[int, int, int]],
+                    sel: Optional[int] = None, sel_mem: int = PT_MEM_DEVICE) -> None:
+    arr = _columns(cols)
+    _check(lib.pt_update_table(ctx, table_id, arr, sel, sel_mem), "pt_update_table", ctx)
+
+
+def _edges(edges) -> "C.Array":
+    arr = (pt_edge * max(len(edges), 1))()
+    for i, e in enumerate(edges):
+        t0, c0, t1, c1 = e[:4]
+        arr[i].t0 = t0
+        arr[i].t1 = t1
+        arr[i].ncols = len(c0)
+        for j in range(len(c0)):
+            arr[i].c0[j] = c0[j]
+            arr[i].c1[j] = c1[j]
+        arr[i].flags = e[4] if len(e) > 4 else 0
+    return arr
+
+
+def pt_set_join_graph(ctx: int, edges: Sequence[tuple]) -> None:
+    """edges: (t0, (cols of t0), t1, (cols of t1)[, flags])."""
+    _check(lib.pt_set_join_graph(ctx, len(edges), _edges(edges)), "pt_set_join_graph", ctx)
+
+
+def pt_plan(ctx: int, n_tables: int) -> Tuple[List[int], int]:
+    order = (C.c_int32 * n_tables)()
+    mem = C.c_int64()
+    _check(lib.pt_plan(ctx, C.cast(order, _P), C.byref(mem)), "pt_plan", ctx)
+    return list(order), mem.value
+
+
+def pt_run_forward(ctx: int) -> None:
+    _check(lib.pt_run_forward(ctx), "pt_run_forward", ctx)
+
+
+def pt_run_backward(ctx: int) -> None:
+    _check(lib.pt_run_backward(ctx), "pt_run_backward", ctx)
+
+
+def pt_run_transfer(ctx: int) -> None:
+    _check(lib.pt_run_transfer(ctx), "pt_run_transfer", ctx)
+
+
+def pt_set_graph_mode(ctx: int, on: bool) -> None:
+    _check(lib.pt_set_graph_mode(ctx, int(on)), "pt_set_graph_mode", ctx)
+
+
+def pt_get_survivors(ctx: int, table_id: int, bitmap_out: Optional[int]) -> int:
+    cnt = C.c_int64()
+    _check(lib.pt_get_survivors(ctx, table_id, bitmap_out, C.byref(cnt)), "pt_get_survivors", ctx)
+    return cnt.value
+
+
+def pt_get_pass_survivors(ctx: int, pass_: int, table_id: int, bitmap_out: Optional[int]) -> int:
+    cnt = C.c_int64()
+    _check(lib.pt_get_pass_survivors(ctx, pass_, table_id, bitmap_out, C.byref(cnt)),
+           "pt_get_pass_survivors", ctx)
+    return cnt.value
+
+
+def pt_get_filter(ctx: int, pass_: int, edge_id: int, words_out: Optional[int]) -> int:
+    nb = C.c_int64()
+    _check(lib.pt_get_filter(ctx, pass_, edge_id, words_out, C.byref(nb)), "pt_get_filter", ctx)
+    return nb.value
+
+
+def pt_get_visit_stats(ctx: int, pass_: int, table_id: int) -> dict:
+    s = pt_visit_stats()
+    _check(lib.pt_get_visit_stats(ctx, pass_, table_id, C.byref(s)), "pt_get_visit_stats", ctx)
+    return {f: getattr(s, f) for f, _ in pt_visit_stats._fields_ if f != "reserved"}
+
+
+def pt_set_launch(ctx: int, threads: int, smem_filter_bytes: int, ctas_per_sm: int = 0) -> None:
+    _check(lib.pt_set_launch(ctx, threads, smem_filter_bytes, ctas_per_sm), "pt_set_launch", ctx)
+
+
+def pt_set_kernel_timing(ctx: int, on: bool) -> None:
+    _check(lib.pt_set_kernel_timing(ctx, int(on)), "pt_set_kernel_timing", ctx)
+
+
+def pt_get_kernel_time(ctx: int) -> dict:
+    sm, om = C.c_double(), C.c_double()
+    sn, on = C.c_int32(), C.c_int32()
+    _check(lib.pt_get_kernel_time(ctx, C.byref(sm), C.byref(sn), C.byref(om), C.byref(on)),
+           "pt_get_kernel_time", ctx)
+    return {"scan_ms": sm.value, "scan_launches": sn.value, "other_ms": om.value,
+            "other_launches": on.value}
+
+
+def pt_get_launch_count(ctx: int) -> int:
+    n = C.c_int64()
+    _check(lib.pt_get_launch_count(ctx, C.byref(n)), "pt_get_launch_count", ctx)
+    return n.value
+
+
+def pt_plan_graph(n_rows: Sequence[int], edges: Sequence[tuple]) -> dict:
+    """Host-only planner: orientation, forward order and levels (no GPU needed)."""
+    nt, ne = len(n_rows), len(edges)
+    nr = (C.c_int64 * nt)(*n_rows)
+    src = (C.c_int32 * max(ne, 1))()
+    dst = (C.c_int32 * max(ne, 1))()
+    order = (C.c_int32 * nt)()
+    level = (C.c_int32 * nt)()
+    _check(lib.pt_plan_graph(nt, C.cast(nr, _P), ne, _edges(edges), C.cast(src, _P), C.cast(dst, _P),
+                             C.cast(order, _P), C.cast(level, _P)), "pt_plan_graph", None)
+    return {"src": list(src)[:ne], "dst": list(dst)[:ne], "order": list(order), "level": list(level)}

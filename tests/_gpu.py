@@ -1,0 +1,72 @@
+"""Run a workloads.Workload through the CUDA library (via the C ABI) and
+collect the same outputs the oracle produces."""
+import numpy as np
+import torch
+
+from paper_2307_15255_b300.session import TransferSession
+
+
+def device_tables(w, host=False, pin=False):
+    tables = []
+    for t in w.tables:
+        cols = []
+        for c in t.cols:
+            x = torch.from_numpy(np.ascontiguousarray(c))
+            cols.append(x.pin_memory() if (host and pin) else (x if host else x.cuda()))
+        sel = None
+        if t.sel is not None:
+            s = torch.from_numpy(np.ascontiguousarray(t.sel).view(np.int32))
+            sel = s.pin_memory() if (host and pin) else (s if host else s.cuda())
+        tables.append((t.n_rows, cols, sel))
+    return tables
+
+
+def edges_of(w):
+    return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1)) for e in w.edges]
+
+
+def session_for(w, launch=None, graph=False, host=False, pin=False):
+    return TransferSession(device_tables(w, host, pin), edges_of(w), w.bits_per_key, w.k, w.block_bits,
+                           w.seed, launch=launch, graph=graph)
+
+
+def collect(s, w):
+    nt, ne = w.n_tables, len(w.edges)
+    out = {"surv": [[None] * nt for _ in range(2)], "count": [[0] * nt for _ in range(2)],
+           "filters": [[None] * ne for _ in range(2)], "nblocks": [[0] * ne for _ in range(2)],
+           "sectors": [[None] * nt for _ in range(2)]}
+    for p in range(2):
+        for v in range(nt):
+            bm, c = s.survivors(v, p)
+            out["surv"][p][v] = bm.cpu().numpy().view(np.uint32)
+            out["count"][p][v] = c
+            st = s.stats(p, v)
+            out["sectors"][p][v] = (st["probe_sectors"], st["build_sectors"])
+        for e in range(ne):
+            f = s.filter(p, e).cpu().numpy().view(np.uint32)
+            out["filters"][p][e] = f
+            out["nblocks"][p][e] = len(f) * 32 // w.block_bits
+    return out
+
+
+def run_gpu(w, **kw):
+    s = session_for(w, **kw)
+    try:
+        s.run()
+        return collect(s, w)
+    finally:
+        s.close()
+
+
+def assert_same(got, want, w, sectors=True):
+    for p in range(2):
+        for v in range(w.n_tables):
+            n = w.tables[v].n_rows
+            g, o = got["surv"][p][v][: (n + 31) // 32], want["surv"][p][v]
+            assert np.array_equal(g, o), f"pass {p} table {v}: survivor bitmaps differ"
+            assert got["count"][p][v] == want["count"][p][v], (p, v)
+            if sectors:
+                assert tuple(got["sectors"][p][v]) == tuple(want["sectors"][p][v]), (p, v)
+        for e in range(len(w.edges)):
+            assert got["nblocks"][p][e] == want["nblocks"][p][e], (p, e)
+            assert np.array_equal(got["filters"][p][e], want["filters"][p][e]), f"pass {p} edge {e}: filters differ"

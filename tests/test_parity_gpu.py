@@ -1,0 +1,169 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU
+oracle: survivor bitmaps and counts of every table after each pass, the
+words and size of every filter built in each pass, and the key-sector
+accounting of every visit."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2307_15255_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _check(w, oracle_lib, **kw):
+    from _gpu import assert_same, run_gpu
+    got = run_gpu(w, **kw)
+    want = oracle_lib.transfer(w)
+    assert_same(got, want, w)
+    return got
+
+
+def test_chain3_full_size(oracle_lib):
+    _check(W.chain3(), oracle_lib)
+
+
+@pytest.mark.parametrize("bpk,k,B", [(10, 4, 256), (8, 4, 256), (16, 4, 512), (10, 7, 512), (3, 1, 256),
+                                     (64, 16, 256)])
+def test_snowflake_small_filter_params(oracle_lib, bpk, k, B):
+    _check(W.snowflake(scale=0.02, bits_per_key=bpk, k=k, block_bits=B), oracle_lib)
+
+
+def test_snowflake_int64_composite_zipf_small(oracle_lib):
+    _check(W.snowflake(scale=0.02, int64=True, composite=True, zipf=1.1, bits_per_key=16), oracle_lib)
+
+
+def test_cyclic_small(oracle_lib):
+    _check(W.cyclic5(scale=0.005), oracle_lib)
+
+
+def test_seeded_hash(oracle_lib):
+    w = W.chain3(scale=0.3)
+    w.seed = 0xDEADBEEF12345678
+    _check(w, oracle_lib)
+
+
+@pytest.mark.parametrize("launch", [(128, 0, 0), (256, 16 * 1024, 0), (512, 0, 2), (1024, 200 * 1024, 1),
+                                    (256, 4 * 1024, 3)])
+def test_launch_shapes_give_identical_results(oracle_lib, launch):
+    # smem budget 0 forces every probe through L1/L2; small budgets split filters between the two
+    _check(W.snowflake(scale=0.03, bits_per_key=16), oracle_lib, launch=launch)
+
+
+def test_random_tiny_graphs(oracle_lib):
+    for s in range(60):
+        w = W.random_tiny(7000 + s, 2 + s % 5, max_rows=200, domain=40, acyclic=(s % 3 != 0),
+                          composite_prob=0.3)
+        _check(w, oracle_lib)
+
+
+def test_edge_cases_sizes(oracle_lib):
+    rng = np.random.default_rng(1)
+    for n_small, n_big in [(0, 5), (1, 1), (31, 33), (32, 64), (1, 1000), (0, 0), (33, 4097)]:
+        a = rng.integers(0, 50, n_small).astype(np.int32)
+        b = rng.integers(0, 50, n_big).astype(np.int64)
+        c = rng.integers(0, 50, n_big + 3).astype(np.int32)
+        A = W.Table("A", n_small, [a], ["k"], W.bitmap_from_bools(rng.random(n_small) < 0.5))
+        Bt = W.Table("B", n_big, [b, b.copy()], ["k", "j"], None)
+        Ct = W.Table("C", n_big + 3, [c], ["j"], W.bitmap_from_bools(rng.random(n_big + 3) < 0.7))
+        lone = W.Table("L", 7, [np.arange(7, dtype=np.int32)], ["x"], None)  # no edges at all
+        w = W.Workload("edge", [A, Bt, Ct, lone], [W.Edge(0, (0,), 1, (0,)), W.Edge(1, (1,), 2, (0,))])
+        _check(w, oracle_lib)
+
+
+def test_empty_and_full_selections(oracle_lib):
+    w = W.chain3(scale=0.1)
+    w.tables[0].sel = np.zeros_like(w.tables[0].sel)
+    _check(w, oracle_lib)
+    w = W.chain3(scale=0.1)
+    w.tables[2].sel = W.bitmap_from_bools(np.ones(w.tables[2].n_rows, bool))
+    _check(w, oracle_lib)
+
+
+def test_graph_mode_host_columns_and_repeat(oracle_lib):
+    from _gpu import assert_same, collect, session_for
+    w = W.snowflake(scale=0.02, int64=True, composite=True, bits_per_key=10)
+    want = oracle_lib.transfer(w)
+    for kw in ({"graph": True}, {"host": True, "pin": True}, {"host": True}):
+        s = session_for(w, **kw)
+        try:
+            for _ in range(3):  # replays and reruns give the same bits
+                s.run()
+                assert_same(collect(s, w), want, w)
+        finally:
+            s.close()
+
+
+def test_update_table_then_rerun(oracle_lib):
+    from _gpu import assert_same, collect, device_tables, session_for
+    w = W.chain3(scale=0.2)
+    s = session_for(w, graph=True)
+    try:
+        s.run()
+        w2 = W.chain3(scale=0.2, seed=99)
+        tabs = device_tables(w2)
+        for v, (n, cols, sel) in enumerate(tabs):
+            s.update(v, cols, sel)
+        s.run()
+        assert_same(collect(s, w2), oracle_lib.transfer(w2), w2)
+    finally:
+        s.close()
+
+
+def test_state_errors():
+    import paper_2307_15255_b300.pt as P
+    ctx = P.pt_create()
+    try:
+        x = torch.arange(10, dtype=torch.int32, device="cuda")
+        P.pt_register_table(ctx, 10, [(x.data_ptr(), P.PT_I32, P.PT_MEM_DEVICE)])
+        with pytest.raises(P.PtError) as ei:
+            P.pt_run_forward(ctx)
+        assert ei.value.status == P.PT_ERR_STATE
+        P.pt_set_join_graph(ctx, [])
+        P.pt_plan(ctx, 1)
+        with pytest.raises(P.PtError) as ei:
+            P.pt_run_backward(ctx)
+        assert ei.value.status == P.PT_ERR_STATE
+        with pytest.raises(P.PtError) as ei:
+            P.pt_get_survivors(ctx, 0, None)
+        assert ei.value.status == P.PT_ERR_STATE
+        with pytest.raises(P.PtError) as ei:
+            P.pt_get_pass_survivors(ctx, 0, 3, None)
+        assert ei.value.status == P.PT_ERR_INVALID
+        P.pt_run_forward(ctx)
+        assert P.pt_get_survivors(ctx, 0, None) == 10
+    finally:
+        P.pt_destroy(ctx)
+
+
+def test_misaligned_device_column_is_rejected():
+    import paper_2307_15255_b300.pt as P
+    ctx = P.pt_create()
+    try:
+        x = torch.arange(16, dtype=torch.int32, device="cuda")
+        with pytest.raises(P.PtError) as ei:
+            P.pt_register_table(ctx, 10, [(x.data_ptr() + 4, P.PT_I32, P.PT_MEM_DEVICE)])
+        assert ei.value.status == P.PT_ERR_INVALID
+    finally:
+        P.pt_destroy(ctx)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg", ["snowflake", "snowflake_x10_b8", "snowflake_x10_b16", "cyclic5"])
+def test_full_size_configs(oracle_lib, cfg):
+    """The full workloads, in the launch shape the benchmark uses, bit for bit."""
+    if cfg == "snowflake":
+        w = W.snowflake()
+    elif cfg.startswith("snowflake_x10"):
+        bpk = 8 if cfg.endswith("b8") else 16
+        w = W.snowflake(scale=10, int64=True, composite=True, zipf=1.1, bits_per_key=bpk)
+    else:
+        w = W.cyclic5()
+    _check(w, oracle_lib)
