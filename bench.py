@@ -41,9 +41,9 @@ FALLBACK_HBM_GBS = 6400.0
 NOMINAL_HBM_GBS = 8000.0
 
 
-def make_workload(name: str, bpk: int):
+def make_workload(name: str, bpk: int, scale: float = 10.0):
     if name == "snowflake_x10":
-        return W.snowflake(scale=10, int64=True, composite=True, zipf=1.1, bits_per_key=bpk)
+        return W.snowflake(scale=scale, int64=True, composite=True, zipf=1.1, bits_per_key=bpk)
     if name == "snowflake":
         return W.snowflake(scale=1, bits_per_key=bpk)
     if name == "cyclic5":
@@ -169,12 +169,12 @@ def reference_arm(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload(args.workload, args.bpk)
+    w = make_workload(args.workload, args.bpk, args.scale)
     rows = visit_rows(w)
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; its first run is already timed like the rest
     import oracle
     oracle.build()
+    for _ in range(args.warmup):
+        oracle.transfer(w)
     # each step: one oracle transfer of the full workload (a few seconds on one core)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -233,7 +233,7 @@ def ours(args) -> None:
     from paper_2307_15255_b300 import pt as P
     from paper_2307_15255_b300.session import TransferSession
 
-    w = make_workload(args.workload, args.bpk)
+    w = make_workload(args.workload, args.bpk, args.scale)
     rows = visit_rows(w)
     tables_dev = []
     for t in w.tables:
@@ -254,6 +254,13 @@ def ours(args) -> None:
     for _ in range(max(args.warmup, 0)):
         s.run()
     torch.cuda.synchronize()
+    if args.only_run:
+        # profiling mode: a few plain transfers, nothing timed or printed
+        for _ in range(args.only_run):
+            s.run()
+        torch.cuda.synchronize()
+        s.close()
+        return
 
     # accounting of one run (identical every step: same inputs)
     acc = {"bitmap": 0, "probe_keys": 0, "build_keys": 0, "ids": 0, "filters": 0}
@@ -395,6 +402,8 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="snowflake_x10")
     ap.add_argument("--bpk", type=int, default=16)
+    ap.add_argument("--scale", type=float, default=10.0, help="size of the snowflake (10 = fact 60M rows)")
+    ap.add_argument("--only-run", type=int, default=0, help="profiling: run this many transfers and exit")
     ap.add_argument("--launch", type=int, nargs=3, metavar=("THREADS", "SMEM", "CTAS_PER_SM"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
