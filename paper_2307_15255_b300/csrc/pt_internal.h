@@ -10,7 +10,14 @@ namespace pt {
 constexpr int kMaxIn = 8;         // incoming edges of one visit
 constexpr int kMaxOut = 8;        // outgoing edges of one visit
 constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
-constexpr int kWordsPerIter = 4;  // bitmap words (32 rows each) a warp scans per iteration
+constexpr int kRoundWords = 32;   // bitmap words (32 rows each) a scan warp takes per round
+constexpr int kQueueCap = 256;    // row-id queue in front of each probe stage (per warp)
+constexpr int kDrain = 128;       // a stage runs once its queue holds this many rows
+
+// Shared memory a scan CTA needs besides its filter budget: per warp, one
+// queue and one 32-word "alive before this probe" bitmap per incoming edge,
+// plus the round's survivor words.
+__host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) { return (size_t)(n_in * (kQueueCap + kRoundWords) + kRoundWords) * 4; }
 
 struct ColRef {
     const void* p;

@@ -100,15 +100,27 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
 
 // ---------------------------------------------------------------------------
 // 1. scan: probe every incoming filter, write the survivor bitmap, compact
+//
+// Each warp owns a contiguous chunk of bitmap words and walks it in rounds
+// of 32 words (1024 rows): one coalesced load brings the round's input
+// words, one per lane.  Rows still alive wait in a per-warp queue in front
+// of each probe stage (incoming edges in probe order); a stage runs once
+// its queue holds 128 rows, four rows per lane, so every probe works on
+// densely packed live rows and each lane has four independent key loads in
+// flight.  Survivors of a stage are appended, in row order, to the next
+// stage's queue; survivors of the last stage set their bit in the round's
+// output words.  At the end of a round the queues are flushed, the 32
+// survivor words are stored, and their row ids are compacted into the
+// warp's segment of the id array with ballot/popc ranks.
 // ---------------------------------------------------------------------------
 template <int B>
 __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
-    extern __shared__ __align__(16) uint32_t s_filt[];
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ProbeEdge s_pe[kMaxIn];     // incoming edges in probe order
-    __shared__ int32_t s_off[kMaxIn];      // word offset in s_filt, or -1: probe from global
+    __shared__ int32_t s_off[kMaxIn];      // word offset of the filter in smem, or -1: probe from global
     __shared__ uint32_t s_nb[kMaxIn];
-    constexpr int U = kWordsPerIter;
     constexpr uint32_t WPB = B / 32;
+    const uint32_t FULL = 0xFFFFFFFFu;
 
     if (threadIdx.x == 0) {
         // LIP-style order: ascending survivors/rows of the building visit, ties by edge id.
@@ -152,10 +164,11 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
         }
     }
     __syncthreads();
-    for (int i = 0; i < a.n_in; ++i) {
+    const int n_in = a.n_in;
+    for (int i = 0; i < n_in; ++i) {
         if (s_off[i] < 0) continue;
         const uint4* src = reinterpret_cast<const uint4*>(s_pe[i].filter);
-        uint4* dst = reinterpret_cast<uint4*>(s_filt + s_off[i]);
+        uint4* dst = reinterpret_cast<uint4*>(smem + s_off[i]);
         const uint32_t n16 = s_nb[i] * (WPB / 4);
         for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
     }
@@ -163,7 +176,13 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t* wsm = smem + a.smem_words + warp * (uint32_t)(scan_warp_smem_bytes(n_in) / 4);
+    uint32_t* queue = wsm;                                  // [n_in][kQueueCap] row ids
+    uint32_t* abm = wsm + n_in * kQueueCap;                 // [n_in][32] rows entering each stage
+    uint32_t* obm = abm + n_in * kRoundWords;               // [32] survivors of the round
+
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const int64_t n_words = (a.n + 31) >> 5;
     const int64_t w_begin = gw * a.words_per_warp;
     const int64_t w_end = min(n_words, w_begin + a.words_per_warp);
@@ -171,89 +190,146 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
     const int k = f.k;
     const uint64_t seed = f.seed;
 
-    uint32_t local = 0;
-    unsigned long long psec = 0, bsec = 0;
+    uint32_t local = 0;                     // survivors of this warp (= its segment length)
+    unsigned long long psec = 0, bsec = 0;  // per lane; reduced at the end
+    // queue lengths, 8 bits per stage in one register (warp-uniform; a queue
+    // never holds more than 255 rows: it is drained below kDrain before each append)
+    uint64_t qpack = 0;
+    auto qget = [&](int s) -> uint32_t { return (uint32_t)(qpack >> (8 * s)) & 0xFFu; };
+    auto qset = [&](int s, uint32_t v) {
+        qpack = (qpack & ~(0xFFull << (8 * s))) | ((uint64_t)v << (8 * s));
+    };
 
-    for (int64_t w0 = w_begin; w0 < w_end; w0 += U) {
-        // input words: lane u loads word w0+u, then broadcast
-        uint32_t mine = 0;
-        if (lane < (uint32_t)U && w0 + lane < w_end) {
-            const int64_t w = w0 + lane;
-            mine = a.in_bits ? __ldg(a.in_bits + w) : 0xFFFFFFFFu;
-            if (w == n_words - 1 && tail_bits) mine &= (1u << tail_bits) - 1u;
+    // Run stage s on the first cnt (<= kDrain) rows of its queue.
+    auto run_stage = [&](int s, uint32_t cnt, uint32_t round_row0) {
+        uint32_t* q = queue + s * kQueueCap;
+        const ColRef c0 = s_pe[s].col[0];
+        const ColRef c1 = s_pe[s].col[1];
+        const int ncols = s_pe[s].ncols;
+        const int32_t off = s_off[s];
+        const uint32_t nb = s_nb[s];
+        const uint32_t* fg = s_pe[s].filter;
+        uint32_t r[4];
+        uint64_t h[4];
+        bool live[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t idx = lane + 32u * i;
+            live[i] = idx < cnt;
+            r[i] = live[i] ? q[idx] : 0u;
         }
-        uint32_t alive[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) alive[u] = __shfl_sync(0xFFFFFFFFu, mine, u);
-
-        for (int j = 0; j < a.n_in; ++j) {
-            uint32_t any = 0;
+        for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(c0, c1, ncols, r[i], seed) : 0ull;
+        bool pass[4];
+        if (off >= 0) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) any |= alive[u];
-            if (!any) break;
-            const ColRef c0 = s_pe[j].col[0];
-            const ColRef c1 = s_pe[j].col[1];
-            const int ncols = s_pe[j].ncols;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                psec += sectors_of(alive[u], c0.dtype);
-                if (ncols == 2) psec += sectors_of(alive[u], c1.dtype);
-            }
-            uint64_t h[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                h[u] = 0;
-                if ((alive[u] >> lane) & 1u) {
-                    const uint32_t r = (uint32_t)((w0 + u) * 32 + lane);
-                    h[u] = edge_hash(c0, c1, ncols, r, seed);
-                }
-            }
-            const int32_t off = s_off[j];
-            const uint32_t nb = s_nb[j];
-            if (off >= 0) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool live = (alive[u] >> lane) & 1u;
-                    const bool pass = live && probe_shared<B>(s_filt, (uint32_t)off, nb, h[u], k);
-                    alive[u] = __ballot_sync(0xFFFFFFFFu, pass);
-                }
-            } else {
-                const uint32_t* fg = s_pe[j].filter;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool live = (alive[u] >> lane) & 1u;
-                    const bool pass = live && probe_global<B>(fg, nb, h[u], k);
-                    alive[u] = __ballot_sync(0xFFFFFFFFu, pass);
-                }
-            }
-        }
-
-        // survivor words: lane u stores word w0+u
-        uint32_t outw = 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (lane == (uint32_t)u) outw = alive[u];
-        if (lane < (uint32_t)U && w0 + lane < w_end) a.out_bits[w0 + lane] = outw;
-
-        if (a.ids) {
-            uint32_t* seg = a.ids + (size_t)w_begin * 32;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t m = alive[u];
-                if ((m >> lane) & 1u) seg[local + __popc(m & lt_mask)] = (uint32_t)((w0 + u) * 32 + lane);
-                local += __popc(m);
-            }
-            for (int b = 0; b < a.n_bcols; ++b) {
-                const int32_t dt = a.bcol[b].dtype;
-#pragma unroll
-                for (int u = 0; u < U; ++u) bsec += sectors_of(alive[u], dt);
-            }
+            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B>(smem, (uint32_t)off, nb, h[i], k);
         } else {
 #pragma unroll
-            for (int u = 0; u < U; ++u) local += __popc(alive[u]);
+            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_global<B>(fg, nb, h[i], k);
         }
+        // keep the unprocessed tail of the queue at its front
+        const uint32_t rest = qget(s) - cnt;
+        uint32_t keep[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t idx = lane + 32u * i;
+            keep[i] = idx < rest ? q[cnt + idx] : 0u;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t idx = lane + 32u * i;
+            if (idx < rest) q[idx] = keep[i];
+        }
+        qset(s, rest);
+        // survivors move on in row order
+        const bool last = s == n_in - 1;
+        uint32_t* nq = queue + (s + 1) * kQueueCap;
+        uint32_t* nbm = last ? obm : abm + (s + 1) * kRoundWords;
+        uint32_t nn = last ? 0u : qget(s + 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t m = __ballot_sync(FULL, pass[i]);
+            if (pass[i]) {
+                atomicOr(nbm + ((r[i] - round_row0) >> 5), 1u << (r[i] & 31));
+                if (!last) nq[nn + __popc(m & lt_mask)] = r[i];
+            }
+            nn += __popc(m);
+        }
+        if (!last) qset(s + 1, nn);
+        __syncwarp();
+    };
+
+    // After stage s ran: later stages whose queue reached kDrain run too.
+    auto cascade = [&](int s, uint32_t round_row0) {
+        for (int t = s + 1; t < n_in; ++t) {
+            if (qget(t) < (uint32_t)kDrain) break;
+            run_stage(t, kDrain, round_row0);
+        }
+    };
+
+    int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
+    for (int64_t rb = w_begin; rb < w_end; rb += kRoundWords) {
+        const int64_t wl = rb + lane;
+        const uint32_t round_row0 = (uint32_t)(rb * 32);
+        uint32_t win = 0;
+        if (wl < w_end) {
+            win = a.in_bits ? __ldg(a.in_bits + wl) : FULL;
+            if (wl == n_words - 1 && tail_bits) win &= (1u << tail_bits) - 1u;
+        }
+        uint32_t ow;
+        if (n_in == 0) {
+            ow = win;
+        } else {
+            obm[lane] = 0u;
+            for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + lane] = s == 0 ? win : 0u;
+            __syncwarp();
+            const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
+            for (int j = 0; j < nw; ++j) {
+                const uint32_t m = __shfl_sync(FULL, win, j);
+                if (!m) continue;
+                const uint32_t q0 = qget(0);
+                if ((m >> lane) & 1u) queue[q0 + __popc(m & lt_mask)] = round_row0 + 32u * j + lane;
+                qset(0, q0 + __popc(m));
+                __syncwarp();
+                if (q0 + __popc(m) >= (uint32_t)kDrain) {
+                    run_stage(0, kDrain, round_row0);
+                    cascade(0, round_row0);
+                }
+            }
+            // flush: every queued row of this round goes through its remaining stages
+            for (int s = 0; s < n_in; ++s) {
+                while (qget(s) > 0) {
+                    run_stage(s, min(qget(s), (uint32_t)kDrain), round_row0);
+                    cascade(s, round_row0);
+                }
+            }
+            __syncwarp();
+            ow = obm[lane];
+            for (int s = 0; s < n_in; ++s) {
+                const uint32_t am = abm[s * kRoundWords + lane];
+                psec += sectors_of(am, s_pe[s].col[0].dtype);
+                if (s_pe[s].ncols == 2) psec += sectors_of(am, s_pe[s].col[1].dtype);
+            }
+            __syncwarp();
+        }
+        if (wl < w_end) a.out_bits[wl] = ow;
+        if (a.ids) {
+            for (int b = 0; b < a.n_bcols; ++b) bsec += sectors_of(ow, a.bcol[b].dtype);
+            const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
+            for (int j = 0; j < nw; ++j) {
+                const uint32_t m = __shfl_sync(FULL, ow, j);
+                if (!m) continue;
+                if ((m >> lane) & 1u) a.ids[seg_pos + __popc(m & lt_mask)] = round_row0 + 32u * j + lane;
+                seg_pos += __popc(m);
+            }
+        }
+        local += __reduce_add_sync(FULL, __popc(ow));
     }
 
+    psec = __reduce_add_sync(FULL, (unsigned)psec);
+    bsec = __reduce_add_sync(FULL, (unsigned)bsec);
     if (lane == 0) {
         if (a.seg_count && gw < a.total_warps) a.seg_count[gw] = local;
         if (local) atomicAdd(a.count, (unsigned long long)local);
@@ -304,19 +380,33 @@ __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const
     for (int64_t s = gw; s < a.total_warps; s += n_warps) {
         const uint32_t cnt = a.seg_count[s];
         const uint32_t* ids = a.ids + (size_t)s * seg_rows;
-        for (uint32_t i = lane; i < cnt; i += 32) {
-            const uint32_t r = ids[i];
+        // four survivors per lane at a time: four independent key gathers in flight
+        for (uint32_t base = 0; base < cnt; base += 128) {
+            uint32_t r[4];
+            bool live[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t idx = base + lane + 32u * i;
+                live[i] = idx < cnt;
+                r[i] = live[i] ? ids[idx] : 0u;
+            }
 #pragma unroll
             for (int e = 0; e < kMaxOut; ++e) {
                 if (e >= a.n_out) break;
                 const BuildEdge& be = a.out[e];
-                const uint64_t h = edge_hash(be.col[0], be.col[1], be.ncols, r, seed);
-                uint32_t* blk = be.filter + (size_t)block_of(h, s_nb[e]) * WPB;
-                const uint32_t lo = (uint32_t)h;
-                const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
-                for (int t = 0; t < k; ++t) {
-                    const uint32_t bit = (h1 + (uint32_t)t * h2) & (B - 1);
-                    atomicOr(blk + (bit >> 5), 1u << (bit & 31));
+                uint64_t h[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(be.col[0], be.col[1], be.ncols, r[i], seed) : 0ull;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (!live[i]) continue;
+                    uint32_t* blk = be.filter + (size_t)block_of(h[i], s_nb[e]) * WPB;
+                    const uint32_t lo = (uint32_t)h[i];
+                    const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
+                    for (int t = 0; t < k; ++t) {
+                        const uint32_t bit = (h1 + (uint32_t)t * h2) & (B - 1);
+                        atomicOr(blk + (bit >> 5), 1u << (bit & 31));
+                    }
                 }
             }
         }

@@ -44,7 +44,8 @@ struct Table {
 // Launch shape of one visit's scan.
 struct ScanShape {
     int grid = 1, block = 256;
-    size_t smem = 0;
+    size_t smem = 0;         // dynamic shared memory: filters + per-warp queues
+    size_t filter_smem = 0;  // the filters' part
     int words_per_warp = 4, total_warps = 8;
 };
 
@@ -86,7 +87,7 @@ struct pt_ctx {
     size_t meta_bytes = 0;
     int64_t seg_cap = 0;
 
-    int scan_threads = 256;
+    int scan_threads = 512;
     int smem_budget = 48 * 1024;
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
@@ -254,21 +255,23 @@ ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
     const int64_t n = ctx->tables[vis.table].n;
     const int64_t n_words = (n + 31) / 32;
     s.block = ctx->scan_threads;
-    const int64_t want_smem = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
-    s.smem = (size_t)((want_smem + 15) / 16 * 16);
+    const int warps_per_cta = s.block / 32;
+    const int64_t want_filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
+    const size_t filt = (size_t)((want_filt + 15) / 16 * 16);
+    s.smem = filt + (size_t)warps_per_cta * pt::scan_warp_smem_bytes((int)vis.in_edges.size());
+    s.filter_smem = filt;
     int fit = pt::scan_max_ctas_per_sm(ctx->fcfg.block_bits, s.block, s.smem);
     if (fit < 1) fit = 1;
     if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
-    const int warps_per_cta = s.block / 32;
     const int64_t max_grid = (int64_t)ctx->num_sms * fit;
-    const int64_t want_warps = (n_words + pt::kWordsPerIter - 1) / pt::kWordsPerIter;
+    const int64_t want_warps = (n_words + pt::kRoundWords - 1) / pt::kRoundWords;  // at least a round each
     int64_t grid = (want_warps + warps_per_cta - 1) / warps_per_cta;
     grid = std::max<int64_t>(1, std::min(grid, max_grid));
     s.grid = (int)grid;
     s.total_warps = (int)(grid * warps_per_cta);
     int64_t wpw = (n_words + s.total_warps - 1) / s.total_warps;
-    wpw = (wpw + pt::kWordsPerIter - 1) / pt::kWordsPerIter * pt::kWordsPerIter;
-    if (wpw < pt::kWordsPerIter) wpw = pt::kWordsPerIter;
+    wpw = (wpw + pt::kRoundWords - 1) / pt::kRoundWords * pt::kRoundWords;
+    if (wpw < pt::kRoundWords) wpw = pt::kRoundWords;
     s.words_per_warp = (int)wpw;
     return s;
 }
@@ -292,7 +295,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     a.n_out = (int)vis.out_edges.size();
     a.words_per_warp = sh.words_per_warp;
     a.total_warps = sh.total_warps;
-    a.smem_words = (int32_t)(sh.smem / 4);
+    a.smem_words = (int32_t)(sh.filter_smem / 4);
     for (int i = 0; i < a.n_in; ++i) {
         const int e = vis.in_edges[i];
         const pt_edge& ed = ctx->edges[e];
@@ -337,8 +340,11 @@ pt_status prepare_shapes(pt_ctx* ctx) {
     if (ctx->shapes_ready) return PT_OK;
     size_t max_smem = 0;
     for (int p = 0; p < 2; ++p)
-        for (Visit& vis : ctx->visits[p]) max_smem = std::max(max_smem, (size_t)((std::min<int64_t>(
-            ctx->smem_budget, vis.in_edges.empty() ? 0 : vis.max_in_filter_bytes) + 15) / 16 * 16));
+        for (Visit& vis : ctx->visits[p]) {
+            const int64_t filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
+            max_smem = std::max(max_smem, (size_t)((filt + 15) / 16 * 16) + (size_t)(ctx->scan_threads / 32) *
+                                                  pt::scan_warp_smem_bytes((int)vis.in_edges.size()));
+        }
     const int bi = ctx->fcfg.block_bits == 512 ? 1 : 0;
     if ((int)max_smem > ctx->smem_attr_set[bi]) {
         PT_CUDA(ctx, pt::scan_set_smem_limit(ctx->fcfg.block_bits, max_smem));
