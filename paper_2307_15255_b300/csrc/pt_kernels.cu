@@ -67,35 +67,39 @@ __device__ __forceinline__ uint32_t sectors_of(uint32_t m, int32_t dtype) {
     return __popc(m & 0x11111111u);
 }
 
-template <int B>
+// Probe one key: all k bits (h1 + i*h2) mod B of its block set?  KT > 0
+// fixes k at compile time (fully unrolled); KT == 0 reads it at run time.
+template <int B, int KT>
 __device__ __forceinline__ bool probe_shared(const uint32_t* s_filt, uint32_t off, uint32_t nb, uint64_t h,
                                              int k) {
     constexpr uint32_t WPB = B / 32;
     const uint32_t base = off + block_of(h, nb) * WPB;
     const uint32_t lo = (uint32_t)h;
     const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
-    bool ok = true;
+    const int kk = KT > 0 ? KT : k;
+    uint32_t ok = 1u;
 #pragma unroll 4
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < kk; ++i) {
         const uint32_t bit = (h1 + (uint32_t)i * h2) & (B - 1);
-        ok &= ((s_filt[base + (bit >> 5)] >> (bit & 31)) & 1u) != 0;
+        ok &= s_filt[base + (bit >> 5)] >> (bit & 31);
     }
-    return ok;
+    return ok & 1u;
 }
 
-template <int B>
+template <int B, int KT>
 __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uint32_t nb, uint64_t h, int k) {
     constexpr uint32_t WPB = B / 32;
     const uint32_t* blk = f + (size_t)block_of(h, nb) * WPB;
     const uint32_t lo = (uint32_t)h;
     const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
-    bool ok = true;
+    const int kk = KT > 0 ? KT : k;
+    uint32_t ok = 1u;
 #pragma unroll 4
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < kk; ++i) {
         const uint32_t bit = (h1 + (uint32_t)i * h2) & (B - 1);
-        ok &= ((__ldg(blk + (bit >> 5)) >> (bit & 31)) & 1u) != 0;
+        ok &= __ldg(blk + (bit >> 5)) >> (bit & 31);
     }
-    return ok;
+    return ok & 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -113,7 +117,7 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
 // survivor words are stored, and their row ids are compacted into the
 // warp's segment of the id array with ballot/popc ranks.
 // ---------------------------------------------------------------------------
-template <int B>
+template <int B, int KT>
 __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ProbeEdge s_pe[kMaxIn];     // incoming edges in probe order
@@ -223,10 +227,10 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
         bool pass[4];
         if (off >= 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B>(smem, (uint32_t)off, nb, h[i], k);
+            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B, KT>(smem, (uint32_t)off, nb, h[i], k);
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_global<B>(fg, nb, h[i], k);
+            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_global<B, KT>(fg, nb, h[i], k);
         }
         // keep the unprocessed tail of the queue at its front
         const uint32_t rest = qget(s) - cnt;
@@ -279,14 +283,69 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
             if (wl == n_words - 1 && tail_bits) win &= (1u << tail_bits) - 1u;
         }
         uint32_t ow;
+        const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
         if (n_in == 0) {
             ow = win;
         } else {
             obm[lane] = 0u;
             for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + lane] = s == 0 ? win : 0u;
             __syncwarp();
-            const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
-            for (int j = 0; j < nw; ++j) {
+            const bool dense = nw == kRoundWords && __all_sync(FULL, win == FULL);
+            if (dense) {
+                // Every row of the round is alive: run stage 0 straight from the
+                // column, 8 rows per lane at a time (rows lane + 32*j, so word j's
+                // survivors are one ballot), with no queue traffic.
+                const ColRef c0 = s_pe[0].col[0];
+                const ColRef c1 = s_pe[0].col[1];
+                const int ncols = s_pe[0].ncols;
+                const int32_t off = s_off[0];
+                const uint32_t nb = s_nb[0];
+                const uint32_t* fg = s_pe[0].filter;
+                const bool last = n_in == 1;
+                uint32_t* nbm = last ? obm : abm + kRoundWords;
+                for (int g = 0; g < kRoundWords; g += 8) {
+                    uint64_t h[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        h[i] = edge_hash(c0, c1, ncols, round_row0 + 32u * (g + i) + lane, seed);
+                    bool pass[8];
+                    if (off >= 0) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(smem, (uint32_t)off, nb, h[i], k);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                    }
+                    uint32_t mk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        mk[i] = __ballot_sync(FULL, pass[i]);
+                        if (lane == 0) nbm[g + i] = mk[i];
+                    }
+                    if (!last) {
+                        // queue the survivors for stage 1, four words at a time so that
+                        // the queue (below kDrain before) never exceeds kQueueCap - 1
+#pragma unroll 1
+                        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                            for (int ii = 0; ii < 4; ++ii) {
+                                const uint32_t m = half ? mk[4 + ii] : mk[ii];
+                                const uint32_t q1 = qget(1);
+                                if ((m >> lane) & 1u)
+                                    queue[kQueueCap + q1 + __popc(m & lt_mask)] =
+                                        round_row0 + 32u * (g + 4 * half + ii) + lane;
+                                qset(1, q1 + __popc(m));
+                            }
+                            __syncwarp();
+                            if (qget(1) >= (uint32_t)kDrain) {
+                                run_stage(1, kDrain, round_row0);
+                                cascade(1, round_row0);
+                            }
+                        }
+                    }
+                }
+            }
+            for (int j = 0; j < (dense ? 0 : nw); ++j) {
                 const uint32_t m = __shfl_sync(FULL, win, j);
                 if (!m) continue;
                 const uint32_t q0 = qget(0);
@@ -317,7 +376,6 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
         if (wl < w_end) a.out_bits[wl] = ow;
         if (a.ids) {
             for (int b = 0; b < a.n_bcols; ++b) bsec += sectors_of(ow, a.bcol[b].dtype);
-            const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
             for (int j = 0; j < nw; ++j) {
                 const uint32_t m = __shfl_sync(FULL, ow, j);
                 if (!m) continue;
@@ -417,10 +475,13 @@ __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const
 
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s) {
-    if (f.block_bits == 512)
-        pt_scan_kernel<512><<<grid, block, smem, s>>>(a, f);
-    else
-        pt_scan_kernel<256><<<grid, block, smem, s>>>(a, f);
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_scan_kernel<512, 4><<<grid, block, smem, s>>>(a, f);
+        else pt_scan_kernel<512, 0><<<grid, block, smem, s>>>(a, f);
+    } else {
+        if (f.k == 4) pt_scan_kernel<256, 4><<<grid, block, smem, s>>>(a, f);
+        else pt_scan_kernel<256, 0><<<grid, block, smem, s>>>(a, f);
+    }
     return cudaGetLastError();
 }
 
@@ -438,18 +499,27 @@ cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int 
 }
 
 int scan_max_ctas_per_sm(int block_bits, int block, size_t smem) {
-    int n = 0;
-    if (block_bits == 512)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_kernel<512>, block, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_kernel<256>, block, smem);
-    return n;
+    int n = 0, m = 0;
+    // every instantiation has the same launch bounds; take the smallest fit
+    if (block_bits == 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_kernel<512, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_kernel<512, 0>, block, smem);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_kernel<256, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_kernel<256, 0>, block, smem);
+    }
+    return n < m ? n : m;
 }
 
 cudaError_t scan_set_smem_limit(int block_bits, size_t smem) {
-    if (block_bits == 512)
-        return cudaFuncSetAttribute(pt_scan_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(pt_scan_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (block_bits == 512) {
+        if ((e = cudaFuncSetAttribute(pt_scan_kernel<512, 4>, at, (int)smem)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(pt_scan_kernel<512, 0>, at, (int)smem);
+    }
+    if ((e = cudaFuncSetAttribute(pt_scan_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pt_scan_kernel<256, 0>, at, (int)smem);
 }
 
 }  // namespace pt
