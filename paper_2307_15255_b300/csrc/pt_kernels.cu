@@ -118,7 +118,7 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
 // warp's segment of the id array with ballot/popc ranks.
 // ---------------------------------------------------------------------------
 template <int B, int KT>
-__global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
+__global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ProbeEdge s_pe[kMaxIn];     // incoming edges in probe order
     __shared__ int32_t s_off[kMaxIn];      // word offset of the filter in smem, or -1: probe from global
@@ -273,15 +273,44 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
         }
     };
 
+    // input words of the round starting at word rb: lane l holds word rb + l
+    auto load_words = [&](int64_t rb) -> uint32_t {
+        const int64_t wl = rb + lane;
+        uint32_t w = 0;
+        if (wl < w_end) {
+            w = a.in_bits ? __ldg(a.in_bits + wl) : FULL;
+            if (wl == n_words - 1 && tail_bits) w &= (1u << tail_bits) - 1u;
+        }
+        return w;
+    };
+    // Dense rounds read stage 0's (single) key column straight from memory:
+    // lane l takes rows lane + 32*j, so word j's survivors are one ballot.
+    // The keys of the next 8 words are loaded before the current 8 are
+    // hashed, and the first 8 of the next round while the current round's
+    // later stages run, so a warp keeps its key loads in flight.
+    const bool dense_ok = n_in > 0 && s_pe[0].ncols == 1;
+    const ColRef d_col = s_pe[0].col[0];
+    auto load8 = [&](uint32_t row0, uint64_t* kv) {
+        if (d_col.dtype == 0) {
+            const int32_t* p = reinterpret_cast<const int32_t*>(d_col.p) + row0 + lane;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)(int64_t)__ldg(p + 32 * i);
+        } else {
+            const long long* p = reinterpret_cast<const long long*>(d_col.p) + row0 + lane;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)__ldg(p + 32 * i);
+        }
+    };
+    uint64_t kn[8];          // prefetched keys (valid when have_pref)
+    bool have_pref = false;
+
     int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
+    uint32_t win = load_words(w_begin);
     for (int64_t rb = w_begin; rb < w_end; rb += kRoundWords) {
         const int64_t wl = rb + lane;
         const uint32_t round_row0 = (uint32_t)(rb * 32);
-        uint32_t win = 0;
-        if (wl < w_end) {
-            win = a.in_bits ? __ldg(a.in_bits + wl) : FULL;
-            if (wl == n_words - 1 && tail_bits) win &= (1u << tail_bits) - 1u;
-        }
+        const int64_t rb_next = rb + kRoundWords;
+        const uint32_t win_next = load_words(rb_next);
         uint32_t ow;
         const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
         if (n_in == 0) {
@@ -290,24 +319,26 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
             obm[lane] = 0u;
             for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + lane] = s == 0 ? win : 0u;
             __syncwarp();
-            const bool dense = nw == kRoundWords && __all_sync(FULL, win == FULL);
+            const bool dense = dense_ok && nw == kRoundWords && __all_sync(FULL, win == FULL);
             if (dense) {
-                // Every row of the round is alive: run stage 0 straight from the
-                // column, 8 rows per lane at a time (rows lane + 32*j, so word j's
-                // survivors are one ballot), with no queue traffic.
-                const ColRef c0 = s_pe[0].col[0];
-                const ColRef c1 = s_pe[0].col[1];
-                const int ncols = s_pe[0].ncols;
                 const int32_t off = s_off[0];
                 const uint32_t nb = s_nb[0];
                 const uint32_t* fg = s_pe[0].filter;
                 const bool last = n_in == 1;
                 uint32_t* nbm = last ? obm : abm + kRoundWords;
+                if (!have_pref) load8(round_row0, kn);
+                const bool next_dense = rb_next + kRoundWords <= w_end && __all_sync(FULL, win_next == FULL);
+#pragma unroll 1
                 for (int g = 0; g < kRoundWords; g += 8) {
                     uint64_t h[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        h[i] = edge_hash(c0, c1, ncols, round_row0 + 32u * (g + i) + lane, seed);
+                    for (int i = 0; i < 8; ++i) h[i] = kn[i];
+                    if (g + 8 < kRoundWords)
+                        load8(round_row0 + 32u * (g + 8), kn);
+                    else if (next_dense)
+                        load8(round_row0 + 32u * kRoundWords, kn);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) h[i] = hash_key(h[i], seed);
                     bool pass[8];
                     if (off >= 0) {
 #pragma unroll
@@ -344,6 +375,7 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
                         }
                     }
                 }
+                have_pref = next_dense;
             }
             for (int j = 0; j < (dense ? 0 : nw); ++j) {
                 const uint32_t m = __shfl_sync(FULL, win, j);
@@ -384,6 +416,7 @@ __global__ void __launch_bounds__(1024) pt_scan_kernel(const VisitArgs a, const 
             }
         }
         local += __reduce_add_sync(FULL, __popc(ow));
+        win = win_next;
     }
 
     psec = __reduce_add_sync(FULL, (unsigned)psec);

@@ -773,7 +773,7 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
 
 pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm) {
     if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
-    if (threads < 128 || threads > 1024 || threads % 32) return fail(ctx, PT_ERR_INVALID, "threads %d", threads);
+    if (threads < 64 || threads > 512 || threads % 32) return fail(ctx, PT_ERR_INVALID, "threads %d (64..512, multiple of 32)", threads);
     if (smem_filter_bytes < 0 || smem_filter_bytes > 220 * 1024) return fail(ctx, PT_ERR_INVALID, "smem %d", smem_filter_bytes);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(ctx, PT_ERR_INVALID, "ctas_per_sm %d", ctas_per_sm);
     ctx->scan_threads = threads;
