@@ -67,37 +67,75 @@ __device__ __forceinline__ uint32_t sectors_of(uint32_t m, int32_t dtype) {
     return __popc(m & 0x11111111u);
 }
 
-// Probe one key: all k bits (h1 + i*h2) mod B of its block set?  KT > 0
-// fixes k at compile time (fully unrolled); KT == 0 reads it at run time.
+// The k bit positions of a key, written so that the index arithmetic runs on
+// the multiply-add pipe and only the final shift and AND use the integer ALU
+// (the scan is bound by the ALU pipe otherwise).  With lo = (uint32)h and
+// h2 = (lo >> 16) | 1, a_i = lo + i*h2 agrees with (h1 + i*h2) mod B in its
+// low log2(B) bits; a_i << (32 - log2 B) puts that bit index in the top
+// log2(B) bits, so its word inside the block is mulhi(a_i << .., B/32) and
+// its bit inside the word is a_i & 31 (the wrap-mode funnel shift uses the
+// low 5 bits of the shift amount).
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_hi(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t rot_r(uint32_t x, uint32_t n) {
+    uint32_t d;
+    asm("shf.r.wrap.b32 %0, %1, %1, %2;" : "=r"(d) : "r"(x), "r"(n));
+    return d;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+    return v;
+}
+
+template <int B>
+struct BlockBits {
+    static constexpr uint32_t LOGB = B == 256 ? 8 : 9;
+    static constexpr uint32_t SCALE = 1u << (32 - LOGB);
+    static constexpr uint32_t WPB = B / 32;
+};
+
+// Probe one key in a filter held in shared memory at byte address sbase
+// (shared window): all k bits of its block set?  KT > 0 fixes k at compile
+// time; KT == 0 reads it at run time.
 template <int B, int KT>
-__device__ __forceinline__ bool probe_shared(const uint32_t* s_filt, uint32_t off, uint32_t nb, uint64_t h,
-                                             int k) {
-    constexpr uint32_t WPB = B / 32;
-    const uint32_t base = off + block_of(h, nb) * WPB;
+__device__ __forceinline__ bool probe_shared(uint32_t sbase, uint32_t nb, uint64_t h, int k) {
+    using BB = BlockBits<B>;
     const uint32_t lo = (uint32_t)h;
-    const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
+    const uint32_t blk = mad_lo(mul_hi((uint32_t)(h >> 32), nb), B / 8, sbase);  // byte address of the block
+    const uint32_t h2 = (lo >> 16) | 1u;
     const int kk = KT > 0 ? KT : k;
-    uint32_t ok = 1u;
+    uint32_t ok = 0xFFFFFFFFu;
 #pragma unroll 4
     for (int i = 0; i < kk; ++i) {
-        const uint32_t bit = (h1 + (uint32_t)i * h2) & (B - 1);
-        ok &= s_filt[base + (bit >> 5)] >> (bit & 31);
+        const uint32_t ai = mad_lo((uint32_t)i, h2, lo);
+        const uint32_t wi = mul_hi(mad_lo(ai, BB::SCALE, 0u), BB::WPB);
+        ok &= rot_r(lds_u32(mad_lo(wi, 4u, blk)), ai);
     }
     return ok & 1u;
 }
 
 template <int B, int KT>
 __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uint32_t nb, uint64_t h, int k) {
-    constexpr uint32_t WPB = B / 32;
-    const uint32_t* blk = f + (size_t)block_of(h, nb) * WPB;
+    using BB = BlockBits<B>;
     const uint32_t lo = (uint32_t)h;
-    const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
+    const uint32_t* blk = f + (size_t)mul_hi((uint32_t)(h >> 32), nb) * BB::WPB;
+    const uint32_t h2 = (lo >> 16) | 1u;
     const int kk = KT > 0 ? KT : k;
-    uint32_t ok = 1u;
+    uint32_t ok = 0xFFFFFFFFu;
 #pragma unroll 4
     for (int i = 0; i < kk; ++i) {
-        const uint32_t bit = (h1 + (uint32_t)i * h2) & (B - 1);
-        ok &= __ldg(blk + (bit >> 5)) >> (bit & 31);
+        const uint32_t ai = mad_lo((uint32_t)i, h2, lo);
+        const uint32_t wi = mul_hi(mad_lo(ai, BB::SCALE, 0u), BB::WPB);
+        ok &= rot_r(__ldg(blk + wi), ai);
     }
     return ok & 1u;
 }
@@ -125,6 +163,7 @@ __global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, cons
     __shared__ uint32_t s_nb[kMaxIn];
     constexpr uint32_t WPB = B / 32;
     const uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);  // shared-window address of the filters
 
     if (threadIdx.x == 0) {
         // LIP-style order: ascending survivors/rows of the building visit, ties by edge id.
@@ -227,7 +266,7 @@ __global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, cons
         bool pass[4];
         if (off >= 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B, KT>(smem, (uint32_t)off, nb, h[i], k);
+            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_global<B, KT>(fg, nb, h[i], k);
@@ -342,7 +381,7 @@ __global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, cons
                     bool pass[8];
                     if (off >= 0) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(smem, (uint32_t)off, nb, h[i], k);
+                        for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
