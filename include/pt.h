@@ -217,8 +217,63 @@ pt_status pt_get_launch_count(pt_ctx* ctx, int64_t* launches);
 pt_status pt_plan_graph(int32_t n_tables, const int64_t* n_rows, int32_t n_edges, const pt_edge* edges,
                         int32_t* src_out, int32_t* dst_out, int32_t* order_out, int32_t* level_out);
 
+/* ---- one visit without any allocation ------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running while a stream is being
+ * captured into a CUDA graph (allocation calls are not allowed there),
+ * engines that give all device memory to their own pool up front, and
+ * services that must not meet an out-of-memory error in the middle of a
+ * query.  pt_visit_static runs one filter transformation (Section 3.2, Fig.
+ * 2) -- probe, survivor bitmap, compaction, size/clear and insert -- with
+ * every input and output supplied by the caller.  Its scratch (compacted
+ * row ids, per-warp segment lengths, counters) is a fixed array of about
+ * 4.1 MB that is part of the library's device image: every GPU that loads
+ * the library holds it until the process exits, and nothing is allocated
+ * per call.
+ *
+ * Limits and rules:
+ *   - n_rows <= PT_STATIC_MAX_ROWS; larger visits return PT_ERR_INVALID.
+ *   - All calls share the one scratch array: calls whose work overlaps on
+ *     the GPU (different streams without ordering, or different host
+ *     threads) race and give wrong results.  Calls on one stream are safe.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture.
+ *   - The survivor count and sector counters are zeroed at the start of
+ *     every call; nothing else carries over between calls.
+ * Incoming filters are probed in the order given.  Key columns, filters and
+ * bitmaps are device memory; filters 16-byte aligned.  Asynchronous on
+ * cuda_stream; errors are reported through pt_last_error(NULL). */
+#define PT_STATIC_MAX_ROWS (1 << 20)
+
+typedef struct {
+    pt_column col[2];       /* this table's key column(s) on the edge (device) */
+    int32_t ncols;          /* 1 or 2 */
+    int32_t reserved;
+    const uint32_t* filter; /* the incoming filter's words (device) */
+    const int64_t* nblocks; /* its size in blocks (device) */
+} pt_static_probe;
+
+typedef struct {
+    pt_column col[2];       /* this table's key column(s) on the edge (device) */
+    int32_t ncols;          /* 1 or 2 */
+    int32_t reserved;
+    uint32_t* filter;       /* output filter words (device, capacity_blocks*block_bits/32) */
+    int64_t capacity_blocks;/* must cover the size rule for n_rows survivors */
+    int64_t probe_rows;     /* rows of the table at the edge's other end */
+    int64_t* nblocks_out;   /* device: blocks the filter uses */
+} pt_static_build;
+
+/* in_bits: input bitmap (device, NULL = every row); out_bits: survivor
+ * bitmap (device, ceil(n_rows/32) words); count_out: device int64 that
+ * receives the survivor count (nullable). */
+pt_status pt_visit_static(const pt_filter_cfg* cfg, void* cuda_stream, int64_t n_rows, const uint32_t* in_bits,
+                          int32_t n_in, const pt_static_probe* in, int32_t n_out, const pt_static_build* out,
+                          uint32_t* out_bits, int64_t* count_out);
+
 /* Message of the last failed call on ctx (or of the last failed pt_create /
- * pt_plan_graph when ctx is NULL).  Valid until the next call on ctx. */
+ * pt_plan_graph / pt_visit_static when ctx is NULL).  Valid until the next
+ * call on ctx. */
 const char* pt_last_error(pt_ctx* ctx);
 
 #ifdef __cplusplus

@@ -82,6 +82,9 @@ cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int bl
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
 cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
 
+// Message returned by pt_last_error(NULL) (calls that have no context).
+void set_global_error(const char* msg);
+
 // CTAs of the scan kernel that fit on one SM for this shape.
 int scan_max_ctas_per_sm(int block_bits, int block, size_t smem);
 cudaError_t scan_set_smem_limit(int block_bits, size_t smem);

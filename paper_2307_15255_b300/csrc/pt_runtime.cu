@@ -406,6 +406,10 @@ pt_status require_plan(pt_ctx* ctx) {
 
 }  // namespace
 
+namespace pt {
+void set_global_error(const char* msg) { g_err = msg; }
+}  // namespace pt
+
 extern "C" {
 
 uint32_t pt_abi_version(void) { return (1u << 16) | 0u; }

@@ -50,6 +50,18 @@ class pt_visit_stats(C.Structure):
                 ("n_out", C.c_int32), ("has_input_bitmap", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pt_static_probe(C.Structure):
+    _fields_ = [("col", pt_column * 2), ("ncols", C.c_int32), ("reserved", C.c_int32), ("filter", C.c_void_p),
+                ("nblocks", C.c_void_p)]
+
+
+class pt_static_build(C.Structure):
+    _fields_ = [("col", pt_column * 2), ("ncols", C.c_int32), ("reserved", C.c_int32), ("filter", C.c_void_p),
+                ("capacity_blocks", C.c_int64), ("probe_rows", C.c_int64), ("nblocks_out", C.c_void_p)]
+
+
+PT_STATIC_MAX_ROWS = 1 << 20
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built (python -m paper_2307_15255_b300.build); "
                       "there is no non-CUDA fallback")
@@ -81,6 +93,8 @@ _SIGS = {
     "pt_get_launch_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "pt_plan_graph": (C.c_int, [C.c_int32, _P, C.c_int32, C.POINTER(pt_edge), _P, _P, _P, _P]),
     "pt_last_error": (C.c_char_p, [_P]),
+    "pt_visit_static": (C.c_int, [C.POINTER(pt_filter_cfg), _P, C.c_int64, _P, C.c_int32,
+                                  C.POINTER(pt_static_probe), C.c_int32, C.POINTER(pt_static_build), _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -226,6 +240,32 @@ def pt_get_launch_count(ctx: int) -> int:
     n = C.c_int64()
     _check(lib.pt_get_launch_count(ctx, C.byref(n)), "pt_get_launch_count", ctx)
     return n.value
+
+
+def pt_visit_static(n_rows: int, in_bits: Optional[int], probes: Sequence[tuple], builds: Sequence[tuple],
+                    out_bits: int, count_out: Optional[int], bits_per_key: int = 10, k: int = 4,
+                    block_bits: int = 256, seed: int = 0, stream: Optional[int] = None) -> None:
+    """One visit with no allocation (see include/pt.h).
+
+    probes: (cols, filter_ptr, nblocks_ptr) with cols a list of (ptr, dtype);
+    builds: (cols, filter_ptr, capacity_blocks, probe_rows, nblocks_out_ptr).
+    All pointers are device pointers.
+    """
+    cfg = pt_filter_cfg(bits_per_key, k, block_bits, 0, seed)
+    pa = (pt_static_probe * max(len(probes), 1))()
+    for i, (cols, fptr, nbptr) in enumerate(probes):
+        pa[i].ncols = len(cols)
+        for j, (ptr, dt) in enumerate(cols):
+            pa[i].col[j].data, pa[i].col[j].dtype, pa[i].col[j].mem = ptr, dt, PT_MEM_DEVICE
+        pa[i].filter, pa[i].nblocks = fptr, nbptr
+    ba = (pt_static_build * max(len(builds), 1))()
+    for i, (cols, fptr, cap, prows, nbout) in enumerate(builds):
+        ba[i].ncols = len(cols)
+        for j, (ptr, dt) in enumerate(cols):
+            ba[i].col[j].data, ba[i].col[j].dtype, ba[i].col[j].mem = ptr, dt, PT_MEM_DEVICE
+        ba[i].filter, ba[i].capacity_blocks, ba[i].probe_rows, ba[i].nblocks_out = fptr, cap, prows, nbout
+    _check(lib.pt_visit_static(C.byref(cfg), stream, n_rows, in_bits, len(probes), pa, len(builds), ba, out_bits,
+                               count_out), "pt_visit_static", None)
 
 
 def pt_plan_graph(n_rows: Sequence[int], edges: Sequence[tuple]) -> dict:
