@@ -189,7 +189,7 @@ pt_status pt_get_filter(pt_ctx* ctx, int32_t pass, int32_t edge_id, uint32_t* wo
 /* Accounting of one visit of the last run of that pass.  Synchronizes. */
 pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_visit_stats* out);
 
-/* Launch shape of the scan kernel: threads per CTA (64..512, multiple of
+/* Launch shape of the scan kernel: threads per CTA (64..256, multiple of
  * 32), shared-memory filter budget per CTA in bytes (0 = probe every filter
  * from L2), and CTAs per SM to aim for (0 = as many as fit).  Takes effect
  * at the next run; invalidates a captured graph. */

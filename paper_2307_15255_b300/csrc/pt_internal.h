@@ -13,6 +13,8 @@ constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
 constexpr int kRoundWords = 32;   // bitmap words (32 rows each) a scan warp takes per round
 constexpr int kQueueCap = 256;    // row-id queue in front of each probe stage (per warp)
 constexpr int kDrain = 128;       // a stage runs once its queue holds this many rows
+constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
+constexpr int kScanMinBlocks = 3;     // scan CTAs per SM the register budget allows
 
 // Shared memory a scan CTA needs besides its filter budget: per warp, one
 // queue and one 32-word "alive before this probe" bitmap per incoming edge,

@@ -48,11 +48,6 @@ __device__ __forceinline__ uint64_t edge_hash(const ColRef& c0, const ColRef& c1
     return hash_key(a, seed);
 }
 
-// Block of a hash: multiply-shift range reduction of its high word.
-__device__ __forceinline__ uint32_t block_of(uint64_t h, uint32_t nblocks) {
-    return __umulhi((uint32_t)(h >> 32), nblocks);
-}
-
 // 32-byte sectors of a column holding at least one set row of a 32-row
 // word: 8 rows per sector for int32 (4 sectors), 4 rows for int64 (8).
 __device__ __forceinline__ uint32_t sectors_of(uint32_t m, int32_t dtype) {
@@ -156,7 +151,7 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
 // warp's segment of the id array with ballot/popc ranks.
 // ---------------------------------------------------------------------------
 template <int B, int KT>
-__global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
+__global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ProbeEdge s_pe[kMaxIn];     // incoming edges in probe order
     __shared__ int32_t s_off[kMaxIn];      // word offset of the filter in smem, or -1: probe from global
@@ -252,53 +247,67 @@ __global__ void __launch_bounds__(512, 1) pt_scan_kernel(const VisitArgs a, cons
         const int32_t off = s_off[s];
         const uint32_t nb = s_nb[s];
         const uint32_t* fg = s_pe[s].filter;
-        uint32_t r[4];
-        uint64_t h[4];
-        bool live[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t idx = lane + 32u * i;
-            live[i] = idx < cnt;
-            r[i] = live[i] ? q[idx] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(c0, c1, ncols, r[i], seed) : 0ull;
-        bool pass[4];
-        if (off >= 0) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pass[i] = live[i] && probe_global<B, KT>(fg, nb, h[i], k);
-        }
-        // keep the unprocessed tail of the queue at its front
-        const uint32_t rest = qget(s) - cnt;
-        uint32_t keep[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t idx = lane + 32u * i;
-            keep[i] = idx < rest ? q[cnt + idx] : 0u;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t idx = lane + 32u * i;
-            if (idx < rest) q[idx] = keep[i];
-        }
-        qset(s, rest);
-        // survivors move on in row order
         const bool last = s == n_in - 1;
         uint32_t* nq = queue + (s + 1) * kQueueCap;
         uint32_t* nbm = last ? obm : abm + (s + 1) * kRoundWords;
         uint32_t nn = last ? 0u : qget(s + 1);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t m = __ballot_sync(FULL, pass[i]);
-            if (pass[i]) {
-                atomicOr(nbm + ((r[i] - round_row0) >> 5), 1u << (r[i] & 31));
-                if (!last) nq[nn + __popc(m & lt_mask)] = r[i];
+        // survivors move on in row order
+        auto emit = [&](bool pass, uint32_t r) {
+            const uint32_t m = __ballot_sync(FULL, pass);
+            if (pass) {
+                atomicOr(nbm + ((r - round_row0) >> 5), 1u << (r & 31));
+                if (!last) nq[nn + __popc(m & lt_mask)] = r;
             }
             nn += __popc(m);
+        };
+        if (cnt == (uint32_t)kDrain) {
+            // a full batch: four rows per lane, four independent gathers in flight
+            uint32_t r[4];
+            uint64_t h[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = q[lane + 32u * i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) h[i] = edge_hash(c0, c1, ncols, r[i], seed);
+            bool pass[4];
+            if (off >= 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+            }
+            // keep the unprocessed tail of the queue at its front
+            const uint32_t rest = qget(s) - cnt;
+            uint32_t keep[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t idx = lane + 32u * i;
+                keep[i] = idx < rest ? q[cnt + idx] : 0u;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t idx = lane + 32u * i;
+                if (idx < rest) q[idx] = keep[i];
+            }
+            qset(s, rest);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) emit(pass[i], r[i]);
+        } else {
+            // the rest of a round (cnt < kDrain is the whole queue): 32 rows at a time
+            for (uint32_t b = 0; b < cnt; b += 32) {
+                const uint32_t idx = b + lane;
+                const bool live = idx < cnt;
+                const uint32_t r = live ? q[idx] : 0u;
+                bool pass = false;
+                if (live) {
+                    const uint64_t h = edge_hash(c0, c1, ncols, r, seed);
+                    pass = off >= 0 ? probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h, k)
+                                    : probe_global<B, KT>(fg, nb, h, k);
+                }
+                emit(pass, r);
+            }
+            qset(s, 0u);
         }
         if (!last) qset(s + 1, nn);
         __syncwarp();
@@ -491,9 +500,9 @@ __global__ void __launch_bounds__(512) pt_size_clear_kernel(const VisitArgs a, c
 // ---------------------------------------------------------------------------
 // 3. insert the survivors' outgoing keys
 // ---------------------------------------------------------------------------
-template <int B>
+template <int B, int KT>
 __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
-    constexpr uint32_t WPB = B / 32;
+    using BB = BlockBits<B>;
     __shared__ uint32_t s_nb[kMaxOut];
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e)
@@ -530,12 +539,34 @@ __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (!live[i]) continue;
-                    uint32_t* blk = be.filter + (size_t)block_of(h[i], s_nb[e]) * WPB;
                     const uint32_t lo = (uint32_t)h[i];
-                    const uint32_t h1 = lo & (B - 1), h2 = (lo >> 16) | 1u;
-                    for (int t = 0; t < k; ++t) {
-                        const uint32_t bit = (h1 + (uint32_t)t * h2) & (B - 1);
-                        atomicOr(blk + (bit >> 5), 1u << (bit & 31));
+                    uint32_t* blk = be.filter + (size_t)mul_hi((uint32_t)(h[i] >> 32), s_nb[e]) * BB::WPB;
+                    const uint32_t h2 = (lo >> 16) | 1u;
+                    if (KT > 0) {
+                        // bits that share a word go out in one atomicOr
+                        uint32_t w[KT > 0 ? KT : 1], m[KT > 0 ? KT : 1];
+#pragma unroll
+                        for (int t = 0; t < KT; ++t) {
+                            const uint32_t at = mad_lo((uint32_t)t, h2, lo);
+                            w[t] = mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB);
+                            m[t] = 1u << (at & 31);
+                        }
+#pragma unroll
+                        for (int t = 1; t < KT; ++t)
+#pragma unroll
+                            for (int u = 0; u < t; ++u)
+                                if (m[t] && w[t] == w[u] && m[u]) {
+                                    m[u] |= m[t];
+                                    m[t] = 0;
+                                }
+#pragma unroll
+                        for (int t = 0; t < KT; ++t)
+                            if (m[t]) atomicOr(blk + w[t], m[t]);
+                    } else {
+                        for (int t = 0; t < k; ++t) {
+                            const uint32_t at = mad_lo((uint32_t)t, h2, lo);
+                            atomicOr(blk + mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB), 1u << (at & 31));
+                        }
                     }
                 }
             }
@@ -563,10 +594,13 @@ cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, 
 }
 
 cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s) {
-    if (f.block_bits == 512)
-        pt_insert_kernel<512><<<grid, block, 0, s>>>(a, f);
-    else
-        pt_insert_kernel<256><<<grid, block, 0, s>>>(a, f);
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_insert_kernel<512, 4><<<grid, block, 0, s>>>(a, f);
+        else pt_insert_kernel<512, 0><<<grid, block, 0, s>>>(a, f);
+    } else {
+        if (f.k == 4) pt_insert_kernel<256, 4><<<grid, block, 0, s>>>(a, f);
+        else pt_insert_kernel<256, 0><<<grid, block, 0, s>>>(a, f);
+    }
     return cudaGetLastError();
 }
 

@@ -87,8 +87,8 @@ struct pt_ctx {
     size_t meta_bytes = 0;
     int64_t seg_cap = 0;
 
-    int scan_threads = 512;
-    int smem_budget = 48 * 1024;
+    int scan_threads = 256;
+    int smem_budget = 40 * 1024;
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
     bool shapes_ready = false;
@@ -777,7 +777,8 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
 
 pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm) {
     if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
-    if (threads < 64 || threads > 512 || threads % 32) return fail(ctx, PT_ERR_INVALID, "threads %d (64..512, multiple of 32)", threads);
+    if (threads < 64 || threads > pt::kScanMaxThreads || threads % 32)
+        return fail(ctx, PT_ERR_INVALID, "threads %d (64..%d, multiple of 32)", threads, pt::kScanMaxThreads);
     if (smem_filter_bytes < 0 || smem_filter_bytes > 220 * 1024) return fail(ctx, PT_ERR_INVALID, "smem %d", smem_filter_bytes);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(ctx, PT_ERR_INVALID, "ctas_per_sm %d", ctas_per_sm);
     ctx->scan_threads = threads;

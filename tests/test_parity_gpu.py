@@ -50,7 +50,7 @@ def test_seeded_hash(oracle_lib):
     _check(w, oracle_lib)
 
 
-@pytest.mark.parametrize("launch", [(128, 0, 0), (256, 16 * 1024, 0), (512, 0, 2), (512, 160 * 1024, 1),
+@pytest.mark.parametrize("launch", [(128, 0, 0), (256, 16 * 1024, 0), (64, 0, 2), (256, 180 * 1024, 1),
                                     (256, 4 * 1024, 3)])
 def test_launch_shapes_give_identical_results(oracle_lib, launch):
     # smem budget 0 forces every probe through L1/L2; small budgets split filters between the two
