@@ -10,14 +10,15 @@ namespace pt {
 constexpr int kMaxIn = 8;         // incoming edges of one visit
 constexpr int kMaxOut = 8;        // outgoing edges of one visit
 constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
-constexpr int kRoundWords = 32;   // bitmap words (32 rows each) a scan warp takes per round
-constexpr int kQueueCap = 256;    // row-id queue in front of each probe stage (per warp)
-constexpr int kDrain = 128;       // a stage runs once its queue holds this many rows
+constexpr int kRoundWords = 128;  // bitmap words (32 rows each) a scan warp takes per round
+constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words
+constexpr int kQueueCap = 128;    // row-id queue in front of each probe stage (per warp)
+constexpr int kDrain = 64;        // a stage runs once its queue holds this many rows
 constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
 constexpr int kScanMinBlocks = 3;     // scan CTAs per SM the register budget allows
 
 // Shared memory a scan CTA needs besides its filter budget: per warp, one
-// queue and one 32-word "alive before this probe" bitmap per incoming edge,
+// queue and one round of "alive before this probe" words per incoming edge,
 // plus the round's survivor words.
 __host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) { return (size_t)(n_in * (kQueueCap + kRoundWords) + kRoundWords) * 4; }
 

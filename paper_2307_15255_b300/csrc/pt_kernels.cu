@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t* wsm = smem + a.smem_words + warp * (uint32_t)(scan_warp_smem_bytes(n_in) / 4);
     uint32_t* queue = wsm;                                  // [n_in][kQueueCap] row ids
-    uint32_t* abm = wsm + n_in * kQueueCap;                 // [n_in][32] rows entering each stage
-    uint32_t* obm = abm + n_in * kRoundWords;               // [32] survivors of the round
+    uint32_t* abm = wsm + n_in * kQueueCap;                 // [n_in][kRoundWords] rows entering each stage
+    uint32_t* obm = abm + n_in * kRoundWords;               // [kRoundWords] survivors of the round
 
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const int64_t n_words = (a.n + 31) >> 5;
@@ -261,38 +261,40 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
             nn += __popc(m);
         };
         if (cnt == (uint32_t)kDrain) {
-            // a full batch: four rows per lane, four independent gathers in flight
-            uint32_t r[4];
-            uint64_t h[4];
+            // a full batch: kDrain/32 rows per lane, independent gathers in flight
+            constexpr int R = kDrain / 32;
+            uint32_t r[R];
+            uint64_t h[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) r[i] = q[lane + 32u * i];
+            for (int i = 0; i < R; ++i) r[i] = q[lane + 32u * i];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) h[i] = edge_hash(c0, c1, ncols, r[i], seed);
-            bool pass[4];
+            for (int i = 0; i < R; ++i) h[i] = edge_hash(c0, c1, ncols, r[i], seed);
+            bool pass[R];
             if (off >= 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+                for (int i = 0; i < R; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                for (int i = 0; i < R; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
             }
-            // keep the unprocessed tail of the queue at its front
+            // keep the unprocessed tail of the queue (fewer than kQueueCap - kDrain rows) at its front
             const uint32_t rest = qget(s) - cnt;
-            uint32_t keep[4];
+            constexpr int RT = (kQueueCap - kDrain) / 32;
+            uint32_t keep[RT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < RT; ++i) {
                 const uint32_t idx = lane + 32u * i;
                 keep[i] = idx < rest ? q[cnt + idx] : 0u;
             }
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < RT; ++i) {
                 const uint32_t idx = lane + 32u * i;
                 if (idx < rest) q[idx] = keep[i];
             }
             qset(s, rest);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) emit(pass[i], r[i]);
+            for (int i = 0; i < R; ++i) emit(pass[i], r[i]);
         } else {
             // the rest of a round (cnt < kDrain is the whole queue): 32 rows at a time
             for (uint32_t b = 0; b < cnt; b += 32) {
@@ -321,21 +323,21 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
         }
     };
 
-    // input words of the round starting at word rb: lane l holds word rb + l
-    auto load_words = [&](int64_t rb) -> uint32_t {
-        const int64_t wl = rb + lane;
-        uint32_t w = 0;
-        if (wl < w_end) {
-            w = a.in_bits ? __ldg(a.in_bits + wl) : FULL;
-            if (wl == n_words - 1 && tail_bits) w &= (1u << tail_bits) - 1u;
+    // Input word w (lane-specific), masked to the table's rows; 0 past the chunk.
+    auto load_word = [&](int64_t w) -> uint32_t {
+        uint32_t x = 0;
+        if (w < w_end) {
+            x = a.in_bits ? __ldg(a.in_bits + w) : FULL;
+            if (w == n_words - 1 && tail_bits) x &= (1u << tail_bits) - 1u;
         }
-        return w;
+        return x;
     };
-    // Dense rounds read stage 0's (single) key column straight from memory:
-    // lane l takes rows lane + 32*j, so word j's survivors are one ballot.
-    // The keys of the next 8 words are loaded before the current 8 are
-    // hashed, and the first 8 of the next round while the current round's
-    // later stages run, so a warp keeps its key loads in flight.
+    // Dense sub-rounds (32 words, every row alive) read stage 0's single key
+    // column straight from memory: lane l takes rows lane + 32*j, so word j's
+    // survivors are one ballot.  The keys of the next 8 words are loaded
+    // before the current 8 are hashed, and the first 8 of the next dense
+    // sub-round before the current one's last 8, so a warp keeps its key
+    // loads in flight.
     const bool dense_ok = n_in > 0 && s_pe[0].ncols == 1;
     const ColRef d_col = s_pe[0].col[0];
     auto load8 = [&](uint32_t row0, uint64_t* kv) {
@@ -349,92 +351,118 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
             for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)__ldg(p + 32 * i);
         }
     };
-    uint64_t kn[8];          // prefetched keys (valid when have_pref)
+    uint64_t kn[8];  // prefetched keys (valid when have_pref)
     bool have_pref = false;
+    constexpr int NS = kRoundWords / 32;  // sub-rounds of 32 words per round
+    // every word of a round's queue-path appends; the queue (below kDrain before) must stay below kQueueCap
+    constexpr int kAppendWords = (kQueueCap - kDrain) / 32;
 
     int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
-    uint32_t win = load_words(w_begin);
+    uint32_t win[NS], win_next[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) win[q] = load_word(w_begin + 32 * q + lane);
     for (int64_t rb = w_begin; rb < w_end; rb += kRoundWords) {
-        const int64_t wl = rb + lane;
         const uint32_t round_row0 = (uint32_t)(rb * 32);
         const int64_t rb_next = rb + kRoundWords;
-        const uint32_t win_next = load_words(rb_next);
-        uint32_t ow;
-        const int nw = (int)min((int64_t)kRoundWords, w_end - rb);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) win_next[q] = load_word(rb_next + 32 * q + lane);
+        uint32_t ow[NS];
         if (n_in == 0) {
-            ow = win;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ow[q] = win[q];
         } else {
-            obm[lane] = 0u;
-            for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + lane] = s == 0 ? win : 0u;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                obm[32 * q + lane] = 0u;
+                for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + 32 * q + lane] = s == 0 ? win[q] : 0u;
+            }
             __syncwarp();
-            const bool dense = dense_ok && nw == kRoundWords && __all_sync(FULL, win == FULL);
-            if (dense) {
-                const int32_t off = s_off[0];
-                const uint32_t nb = s_nb[0];
-                const uint32_t* fg = s_pe[0].filter;
-                const bool last = n_in == 1;
-                uint32_t* nbm = last ? obm : abm + kRoundWords;
-                if (!have_pref) load8(round_row0, kn);
-                const bool next_dense = rb_next + kRoundWords <= w_end && __all_sync(FULL, win_next == FULL);
 #pragma unroll 1
-                for (int g = 0; g < kRoundWords; g += 8) {
-                    uint64_t h[8];
+            for (int q = 0; q < NS; ++q) {
+                const int64_t sb = rb + 32 * q;  // first word of the sub-round
+                if (sb >= w_end) break;
+                const int nw = (int)min((int64_t)32, w_end - sb);
+                uint32_t wq = win[0], wn = win[NS > 1 ? 1 : 0];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) h[i] = kn[i];
-                    if (g + 8 < kRoundWords)
-                        load8(round_row0 + 32u * (g + 8), kn);
-                    else if (next_dense)
-                        load8(round_row0 + 32u * kRoundWords, kn);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) h[i] = hash_key(h[i], seed);
-                    bool pass[8];
-                    if (off >= 0) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                for (int t = 1; t < NS; ++t)
+                    if (q == t) {
+                        wq = win[t];
+                        wn = t + 1 < NS ? win[t + 1 < NS ? t + 1 : 0] : win_next[0];
                     }
-                    uint32_t mk[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        mk[i] = __ballot_sync(FULL, pass[i]);
-                        if (lane == 0) nbm[g + i] = mk[i];
-                    }
-                    if (!last) {
-                        // queue the survivors for stage 1, four words at a time so that
-                        // the queue (below kDrain before) never exceeds kQueueCap - 1
+                if (NS == 1) wn = win_next[0];
+                const uint32_t sub_row0 = round_row0 + 1024u * q;
+                const bool dense = dense_ok && nw == 32 && __all_sync(FULL, wq == FULL);
+                if (dense) {
+                    const int32_t off = s_off[0];
+                    const uint32_t nb = s_nb[0];
+                    const uint32_t* fg = s_pe[0].filter;
+                    const bool last = n_in == 1;
+                    uint32_t* nbm = (last ? obm : abm + kRoundWords) + 32 * q;
+                    if (!have_pref) load8(sub_row0, kn);
+                    const bool next_dense = sb + 64 <= w_end && __all_sync(FULL, wn == FULL);
 #pragma unroll 1
-                        for (int half = 0; half < 2; ++half) {
+                    for (int g = 0; g < 32; g += 8) {
+                        uint64_t h[8];
 #pragma unroll
-                            for (int ii = 0; ii < 4; ++ii) {
-                                const uint32_t m = half ? mk[4 + ii] : mk[ii];
-                                const uint32_t q1 = qget(1);
-                                if ((m >> lane) & 1u)
-                                    queue[kQueueCap + q1 + __popc(m & lt_mask)] =
-                                        round_row0 + 32u * (g + 4 * half + ii) + lane;
-                                qset(1, q1 + __popc(m));
-                            }
-                            __syncwarp();
-                            if (qget(1) >= (uint32_t)kDrain) {
-                                run_stage(1, kDrain, round_row0);
-                                cascade(1, round_row0);
+                        for (int i = 0; i < 8; ++i) h[i] = kn[i];
+                        if (g + 8 < 32)
+                            load8(sub_row0 + 32u * (g + 8), kn);
+                        else if (next_dense)
+                            load8(sub_row0 + 1024u, kn);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) h[i] = hash_key(h[i], seed);
+                        bool pass[8];
+                        if (off >= 0) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                        }
+                        uint32_t mk[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            mk[i] = __ballot_sync(FULL, pass[i]);
+                            if (lane == 0) nbm[g + i] = mk[i];
+                        }
+                        if (!last) {
+                            // queue the survivors for stage 1, kAppendWords words at a time
+#pragma unroll 1
+                            for (int part = 0; part < 8 / kAppendWords; ++part) {
+#pragma unroll
+                                for (int ii = 0; ii < kAppendWords; ++ii) {
+                                    uint32_t m = mk[0];
+#pragma unroll
+                                    for (int t = 1; t < 8; ++t)
+                                        if (part * kAppendWords + ii == t) m = mk[t];
+                                    const uint32_t q1 = qget(1);
+                                    if ((m >> lane) & 1u)
+                                        queue[kQueueCap + q1 + __popc(m & lt_mask)] =
+                                            sub_row0 + 32u * (g + part * kAppendWords + ii) + lane;
+                                    qset(1, q1 + __popc(m));
+                                }
+                                __syncwarp();
+                                if (qget(1) >= (uint32_t)kDrain) {
+                                    run_stage(1, kDrain, round_row0);
+                                    cascade(1, round_row0);
+                                }
                             }
                         }
                     }
-                }
-                have_pref = next_dense;
-            }
-            for (int j = 0; j < (dense ? 0 : nw); ++j) {
-                const uint32_t m = __shfl_sync(FULL, win, j);
-                if (!m) continue;
-                const uint32_t q0 = qget(0);
-                if ((m >> lane) & 1u) queue[q0 + __popc(m & lt_mask)] = round_row0 + 32u * j + lane;
-                qset(0, q0 + __popc(m));
-                __syncwarp();
-                if (q0 + __popc(m) >= (uint32_t)kDrain) {
-                    run_stage(0, kDrain, round_row0);
-                    cascade(0, round_row0);
+                    have_pref = next_dense;
+                } else {
+                    for (int j = 0; j < nw; ++j) {
+                        const uint32_t m = __shfl_sync(FULL, wq, j);
+                        if (!m) continue;
+                        const uint32_t q0 = qget(0);
+                        if ((m >> lane) & 1u) queue[q0 + __popc(m & lt_mask)] = sub_row0 + 32u * j + lane;
+                        qset(0, q0 + __popc(m));
+                        __syncwarp();
+                        if (q0 + __popc(m) >= (uint32_t)kDrain) {
+                            run_stage(0, kDrain, round_row0);
+                            cascade(0, round_row0);
+                        }
+                    }
                 }
             }
             // flush: every queued row of this round goes through its remaining stages
@@ -445,26 +473,49 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
                 }
             }
             __syncwarp();
-            ow = obm[lane];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ow[q] = obm[32 * q + lane];
             for (int s = 0; s < n_in; ++s) {
-                const uint32_t am = abm[s * kRoundWords + lane];
-                psec += sectors_of(am, s_pe[s].col[0].dtype);
-                if (s_pe[s].ncols == 2) psec += sectors_of(am, s_pe[s].col[1].dtype);
+                const int32_t d0 = s_pe[s].col[0].dtype, d1 = s_pe[s].col[1].dtype;
+                const bool two = s_pe[s].ncols == 2;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const uint32_t am = abm[s * kRoundWords + 32 * q + lane];
+                    psec += sectors_of(am, d0);
+                    if (two) psec += sectors_of(am, d1);
+                }
             }
             __syncwarp();
         }
-        if (wl < w_end) a.out_bits[wl] = ow;
+        uint32_t pc = 0;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t wl = rb + 32 * q + lane;
+            if (wl < w_end) a.out_bits[wl] = ow[q];
+            pc += __popc(ow[q]);
+        }
         if (a.ids) {
-            for (int b = 0; b < a.n_bcols; ++b) bsec += sectors_of(ow, a.bcol[b].dtype);
-            for (int j = 0; j < nw; ++j) {
-                const uint32_t m = __shfl_sync(FULL, ow, j);
-                if (!m) continue;
-                if ((m >> lane) & 1u) a.ids[seg_pos + __popc(m & lt_mask)] = round_row0 + 32u * j + lane;
-                seg_pos += __popc(m);
+            for (int b = 0; b < a.n_bcols; ++b) {
+                const int32_t dt = a.bcol[b].dtype;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) bsec += sectors_of(ow[q], dt);
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int64_t sb = rb + 32 * q;
+                const int nw = (int)max((int64_t)0, min((int64_t)32, w_end - sb));
+                for (int j = 0; j < nw; ++j) {
+                    const uint32_t m = __shfl_sync(FULL, ow[q], j);
+                    if (!m) continue;
+                    if ((m >> lane) & 1u)
+                        a.ids[seg_pos + __popc(m & lt_mask)] = round_row0 + 1024u * q + 32u * j + lane;
+                    seg_pos += __popc(m);
+                }
             }
         }
-        local += __reduce_add_sync(FULL, __popc(ow));
-        win = win_next;
+        local += __reduce_add_sync(FULL, pc);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) win[q] = win_next[q];
     }
 
     psec = __reduce_add_sync(FULL, (unsigned)psec);

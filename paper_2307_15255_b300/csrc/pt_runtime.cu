@@ -264,14 +264,14 @@ ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
     if (fit < 1) fit = 1;
     if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
     const int64_t max_grid = (int64_t)ctx->num_sms * fit;
-    const int64_t want_warps = (n_words + pt::kRoundWords - 1) / pt::kRoundWords;  // at least a round each
+    const int64_t want_warps = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;  // at least a round each
     int64_t grid = (want_warps + warps_per_cta - 1) / warps_per_cta;
     grid = std::max<int64_t>(1, std::min(grid, max_grid));
     s.grid = (int)grid;
     s.total_warps = (int)(grid * warps_per_cta);
     int64_t wpw = (n_words + s.total_warps - 1) / s.total_warps;
-    wpw = (wpw + pt::kRoundWords - 1) / pt::kRoundWords * pt::kRoundWords;
-    if (wpw < pt::kRoundWords) wpw = pt::kRoundWords;
+    wpw = (wpw + pt::kChunkWords - 1) / pt::kChunkWords * pt::kChunkWords;
+    if (wpw < pt::kChunkWords) wpw = pt::kChunkWords;
     s.words_per_warp = (int)wpw;
     return s;
 }

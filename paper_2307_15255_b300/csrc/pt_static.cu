@@ -142,15 +142,15 @@ extern "C" pt_status pt_visit_static(const pt_filter_cfg* cfg, void* cuda_stream
     int fit = pt::scan_max_ctas_per_sm(cfg->block_bits, block, smem);
     if (fit < 1) fit = 1;
     const int64_t n_words = (n_rows + 31) / 32;
-    int64_t grid = (n_words + pt::kRoundWords - 1) / pt::kRoundWords;
+    int64_t grid = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;
     grid = (grid + warps_per_cta - 1) / warps_per_cta;
     if (grid < 1) grid = 1;
     if (grid > (int64_t)sms * fit) grid = (int64_t)sms * fit;
     while (grid * warps_per_cta > kStaticMaxWarps) --grid;
     const int total_warps = (int)(grid * warps_per_cta);
     int64_t wpw = (n_words + total_warps - 1) / total_warps;
-    wpw = (wpw + pt::kRoundWords - 1) / pt::kRoundWords * pt::kRoundWords;
-    if (wpw < pt::kRoundWords) wpw = pt::kRoundWords;
+    wpw = (wpw + pt::kChunkWords - 1) / pt::kChunkWords * pt::kChunkWords;
+    if (wpw < pt::kChunkWords) wpw = pt::kChunkWords;
 
     pt::VisitArgs a;
     std::memset(&a, 0, sizeof a);
