@@ -12,15 +12,22 @@ constexpr int kMaxOut = 8;        // outgoing edges of one visit
 constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
 constexpr int kRoundWords = 128;  // bitmap words (32 rows each) a scan warp takes per round
 constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words
-constexpr int kQueueCap = 128;    // row-id queue in front of each probe stage (per warp)
-constexpr int kDrain = 64;        // a stage runs once its queue holds this many rows
+constexpr int kDrain = 64;        // a probe stage runs once its queue holds this many rows
+constexpr int kQueueCap = 128;    // row-id queue in front of a probe stage (per warp) ...
+constexpr int kQueueCapBig = 320; // ... except stage 1's, which takes 8 dense words (256 rows) at once
 constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
-constexpr int kScanMinBlocks = 3;     // scan CTAs per SM the register budget allows
+constexpr int kScanMinBlocks = 2;     // scan CTAs per SM the register budget allows
+
+// Word offset of stage s's queue inside a warp's queue area, and the area's size.
+__host__ __device__ inline int qoff(int s) { return s * kQueueCap + (s >= 2 ? kQueueCapBig - kQueueCap : 0); }
+__host__ __device__ inline int scan_queue_words(int n_in) { return n_in == 0 ? 0 : qoff(n_in - 1) + (n_in == 2 ? kQueueCapBig : kQueueCap); }
 
 // Shared memory a scan CTA needs besides its filter budget: per warp, one
 // queue and one round of "alive before this probe" words per incoming edge,
 // plus the round's survivor words.
-__host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) { return (size_t)(n_in * (kQueueCap + kRoundWords) + kRoundWords) * 4; }
+__host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) {
+    return (size_t)(scan_queue_words(n_in) + n_in * kRoundWords + kRoundWords) * 4;
+}
 
 struct ColRef {
     const void* p;

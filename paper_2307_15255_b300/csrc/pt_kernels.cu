@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t* wsm = smem + a.smem_words + warp * (uint32_t)(scan_warp_smem_bytes(n_in) / 4);
-    uint32_t* queue = wsm;                                  // [n_in][kQueueCap] row ids
-    uint32_t* abm = wsm + n_in * kQueueCap;                 // [n_in][kRoundWords] rows entering each stage
+    uint32_t* queue = wsm;                                  // row-id queues, stage s at qoff(s)
+    uint32_t* abm = wsm + scan_queue_words(n_in);          // [n_in][kRoundWords] rows entering each stage
     uint32_t* obm = abm + n_in * kRoundWords;               // [kRoundWords] survivors of the round
 
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
 
     // Run stage s on the first cnt (<= kDrain) rows of its queue.
     auto run_stage = [&](int s, uint32_t cnt, uint32_t round_row0) {
-        uint32_t* q = queue + s * kQueueCap;
+        uint32_t* q = queue + qoff(s);
         const ColRef c0 = s_pe[s].col[0];
         const ColRef c1 = s_pe[s].col[1];
         const int ncols = s_pe[s].ncols;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
         const uint32_t nb = s_nb[s];
         const uint32_t* fg = s_pe[s].filter;
         const bool last = s == n_in - 1;
-        uint32_t* nq = queue + (s + 1) * kQueueCap;
+        uint32_t* nq = queue + qoff(s + 1);
         uint32_t* nbm = last ? obm : abm + (s + 1) * kRoundWords;
         uint32_t nn = last ? 0u : qget(s + 1);
         // survivors move on in row order
@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
 #pragma unroll
                 for (int i = 0; i < R; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
             }
-            // keep the unprocessed tail of the queue (fewer than kQueueCap - kDrain rows) at its front
+            // keep the unprocessed tail of the queue (fewer than kQueueCapBig - kDrain rows) at its front
             const uint32_t rest = qget(s) - cnt;
-            constexpr int RT = (kQueueCap - kDrain) / 32;
+            constexpr int RT = (kQueueCapBig - kDrain) / 32;
             uint32_t keep[RT];
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
@@ -354,8 +354,6 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
     uint64_t kn[8];  // prefetched keys (valid when have_pref)
     bool have_pref = false;
     constexpr int NS = kRoundWords / 32;  // sub-rounds of 32 words per round
-    // every word of a round's queue-path appends; the queue (below kDrain before) must stay below kQueueCap
-    constexpr int kAppendWords = (kQueueCap - kDrain) / 32;
 
     int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
     uint32_t win[NS], win_next[NS];
@@ -426,26 +424,19 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
                             if (lane == 0) nbm[g + i] = mk[i];
                         }
                         if (!last) {
-                            // queue the survivors for stage 1, kAppendWords words at a time
-#pragma unroll 1
-                            for (int part = 0; part < 8 / kAppendWords; ++part) {
+                            // queue the survivors of all 8 words for stage 1 at once (prefix
+                            // of the words' popcounts + rank inside the word), then drain it
+                            uint32_t q1 = qget(1);
 #pragma unroll
-                                for (int ii = 0; ii < kAppendWords; ++ii) {
-                                    uint32_t m = mk[0];
-#pragma unroll
-                                    for (int t = 1; t < 8; ++t)
-                                        if (part * kAppendWords + ii == t) m = mk[t];
-                                    const uint32_t q1 = qget(1);
-                                    if ((m >> lane) & 1u)
-                                        queue[kQueueCap + q1 + __popc(m & lt_mask)] =
-                                            sub_row0 + 32u * (g + part * kAppendWords + ii) + lane;
-                                    qset(1, q1 + __popc(m));
-                                }
-                                __syncwarp();
-                                if (qget(1) >= (uint32_t)kDrain) {
-                                    run_stage(1, kDrain, round_row0);
-                                    cascade(1, round_row0);
-                                }
+                            for (int i = 0; i < 8; ++i) {
+                                if (pass[i]) queue[qoff(1) + q1 + __popc(mk[i] & lt_mask)] = sub_row0 + 32u * (g + i) + lane;
+                                q1 += __popc(mk[i]);
+                            }
+                            qset(1, q1);
+                            __syncwarp();
+                            while (qget(1) >= (uint32_t)kDrain) {
+                                run_stage(1, kDrain, round_row0);
+                                cascade(1, round_row0);
                             }
                         }
                     }
