@@ -442,9 +442,11 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
                     }
                     have_pref = next_dense;
                 } else {
-                    for (int j = 0; j < nw; ++j) {
+                    uint32_t nz = __ballot_sync(FULL, wq != 0u && lane < (uint32_t)nw);
+                    while (nz) {
+                        const int j = __ffs(nz) - 1;
+                        nz &= nz - 1u;
                         const uint32_t m = __shfl_sync(FULL, wq, j);
-                        if (!m) continue;
                         const uint32_t q0 = qget(0);
                         if ((m >> lane) & 1u) queue[q0 + __popc(m & lt_mask)] = sub_row0 + 32u * j + lane;
                         qset(0, q0 + __popc(m));
@@ -493,11 +495,12 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                const int64_t sb = rb + 32 * q;
-                const int nw = (int)max((int64_t)0, min((int64_t)32, w_end - sb));
-                for (int j = 0; j < nw; ++j) {
+                // only the words that hold survivors (words past the chunk are zero)
+                uint32_t nz = __ballot_sync(FULL, ow[q] != 0u);
+                while (nz) {
+                    const int j = __ffs(nz) - 1;
+                    nz &= nz - 1u;
                     const uint32_t m = __shfl_sync(FULL, ow[q], j);
-                    if (!m) continue;
                     if ((m >> lane) & 1u)
                         a.ids[seg_pos + __popc(m & lt_mask)] = round_row0 + 1024u * q + 32u * j + lane;
                     seg_pos += __popc(m);

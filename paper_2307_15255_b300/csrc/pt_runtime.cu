@@ -106,6 +106,15 @@ struct pt_ctx {
 
     int64_t launches = 0;
     std::string err;
+
+    // Visits of one DAG level run concurrently: each visit is enqueued on one
+    // of these streams and waits on the events of the visits that build its
+    // incoming filters; every pass forks from and joins back into `stream`.
+    static constexpr int kAux = 3;
+    cudaStream_t aux[kAux] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> vev[2];  // per pass, per table: the visit's work is done
+    cudaEvent_t pass_ev[2] = {nullptr, nullptr};
+    std::vector<int> slot[2];         // per pass, per table: position inside its level
 };
 
 namespace {
@@ -356,7 +365,7 @@ pt_status prepare_shapes(pt_ctx* ctx) {
     return PT_OK;
 }
 
-pt_status record_event(pt_ctx* ctx, int kind) {
+pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st) {
     if (!ctx->timing) return PT_OK;
     if (ctx->ev_used == ctx->ev.size()) {
         cudaEvent_t e;
@@ -365,7 +374,7 @@ pt_status record_event(pt_ctx* ctx, int kind) {
         ctx->ev_kind.push_back(0);
     }
     ctx->ev_kind[ctx->ev_used] = kind;
-    PT_CUDA(ctx, cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+    PT_CUDA(ctx, cudaEventRecord(ctx->ev[ctx->ev_used], st));
     ctx->ev_used++;
     return PT_OK;
 }
@@ -373,28 +382,39 @@ pt_status record_event(pt_ctx* ctx, int kind) {
 pt_status enqueue_pass(pt_ctx* ctx, int p) {
     if (!ctx->shapes_ready) return fail(ctx, PT_ERR_STATE, "launch shapes not prepared");
     PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
+    PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
     for (const Visit& vis : ctx->visits[p]) {
+        const int v = vis.table;
+        cudaStream_t st = ctx->aux[ctx->slot[p][v] % pt_ctx::kAux];
+        PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
+        for (int e : vis.in_edges) {
+            const int b = p == 0 ? ctx->src[e] : ctx->dst[e];  // the table that built the filter
+            PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[p][b], 0));
+        }
         const ScanShape& sh = vis.shape;
         pt::VisitArgs a;
         fill_visit_args(ctx, p, vis, sh, a);
-        pt_status st;
-        if ((st = record_event(ctx, 0)) != PT_OK) return st;
-        PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, ctx->stream));
-        if ((st = record_event(ctx, 0)) != PT_OK) return st;
+        pt_status s1;
+        if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
+        PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st));
+        if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
         ctx->launches++;
         if (a.n_out > 0) {
             int64_t words = 0;
             for (int e : vis.out_edges) words = std::max(words, ctx->filt_max_words[e]);
             const int64_t n16 = words / 4;
             int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
-            if ((st = record_event(ctx, 1)) != PT_OK) return st;
-            PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, ctx->stream));
+            if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
+            PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
             const int grid_i = std::max(1, std::min(sh.total_warps / 16 + 1, ctx->num_sms * 4));
-            PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, ctx->stream));
-            if ((st = record_event(ctx, 1)) != PT_OK) return st;
+            PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, st));
+            if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
             ctx->launches += 2;
         }
+        PT_CUDA(ctx, cudaEventRecord(ctx->vev[p][v], st));
     }
+    // join: the pass is complete on the context stream
+    for (const Visit& vis : ctx->visits[p]) PT_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->vev[p][vis.table], 0));
     return PT_OK;
 }
 
@@ -461,6 +481,13 @@ pt_status pt_destroy(pt_ctx* ctx) {
         if (t.sel_owned) cudaFree(t.sel_owned);
     }
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (int p = 0; p < 2; ++p) {
+        for (cudaEvent_t e : ctx->vev[p])
+            if (e) cudaEventDestroy(e);
+        if (ctx->pass_ev[p]) cudaEventDestroy(ctx->pass_ev[p]);
+    }
+    for (int i = 0; i < pt_ctx::kAux; ++i)
+        if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PT_OK;
@@ -565,6 +592,29 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                 return fail(ctx, PT_ERR_UNSUPPORTED, "table %d has more than %d incoming or %d outgoing edges in a pass",
                             vis.table, pt::kMaxIn, pt::kMaxOut);
             ctx->visits[p].push_back(vis);
+        }
+    }
+
+    // streams and events for concurrent visits; slot = position of a visit
+    // among the visits of its level (level = longest path from a source of
+    // that pass's DAG)
+    for (int i = 0; i < pt_ctx::kAux; ++i)
+        if (!ctx->aux[i]) PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
+    for (int p = 0; p < 2; ++p) {
+        if (!ctx->pass_ev[p]) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pass_ev[p], cudaEventDisableTiming));
+        ctx->vev[p].assign(T, nullptr);
+        for (int v = 0; v < T; ++v) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->vev[p][v], cudaEventDisableTiming));
+        std::vector<int> lvl(T, 0), used;
+        for (const Visit& vis : ctx->visits[p])
+            for (int e : vis.out_edges) {
+                const int to = p == 0 ? ctx->dst[e] : ctx->src[e];
+                lvl[to] = std::max(lvl[to], lvl[vis.table] + 1);
+            }
+        ctx->slot[p].assign(T, 0);
+        for (const Visit& vis : ctx->visits[p]) {
+            const int l = lvl[vis.table];
+            if ((int)used.size() <= l) used.resize(l + 1, 0);
+            ctx->slot[p][vis.table] = used[l]++;
         }
     }
 
@@ -688,9 +738,9 @@ pt_status pt_run_transfer(pt_ctx* ctx) {
             return fail(ctx, PT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
         }
     }
-    if ((st = record_event(ctx, 2)) != PT_OK) return st;
+    if ((st = record_event(ctx, 2, ctx->stream)) != PT_OK) return st;
     PT_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
-    if ((st = record_event(ctx, 2)) != PT_OK) return st;
+    if ((st = record_event(ctx, 2, ctx->stream)) != PT_OK) return st;
     ctx->launches += ctx->graph_kernels;
     ctx->passes_done = 3;
     return PT_OK;
