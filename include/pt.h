@@ -195,11 +195,13 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
  * at the next run; invalidates a captured graph. */
 pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm);
 
-/* Kernel timing.  pt_set_kernel_timing(ctx, 1) starts recording CUDA
- * events on the context's stream around every scan (probe + compact)
- * launch and around every visit's size/clear + insert pair (or, in graph
- * mode, around each graph launch); pt_get_kernel_time returns the summed
- * milliseconds and launch counts since timing was last switched on or off.
+/* Kernel timing.  pt_set_kernel_timing(ctx, 1) records CUDA events around
+ * every scan (probe + compact) launch and around every visit's size/clear +
+ * insert pair, on the stream each runs on.  Direct launches accumulate
+ * from the moment timing is switched on.  In graph mode the events are
+ * part of the captured graph (external event-record nodes; switching timing
+ * recaptures), so their values are those of the most recent replay.
+ * pt_get_kernel_time returns the summed milliseconds and counts of both.
  * Synchronizes the context's stream. */
 pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on);
 pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,

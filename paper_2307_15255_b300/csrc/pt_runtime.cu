@@ -103,6 +103,13 @@ struct pt_ctx {
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;
     size_t ev_used = 0;
+    // events captured into the graph as external event nodes (graph mode with timing)
+    bool capturing = false;
+    bool graph_timed = false;
+    std::vector<cudaEvent_t> gev;
+    std::vector<int> gev_kind;
+    size_t gev_used = 0;
+    int64_t graph_replays = 0;
 
     int64_t launches = 0;
     std::string err;
@@ -367,15 +374,21 @@ pt_status prepare_shapes(pt_ctx* ctx) {
 
 pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st) {
     if (!ctx->timing) return PT_OK;
-    if (ctx->ev_used == ctx->ev.size()) {
+    std::vector<cudaEvent_t>& ev = ctx->capturing ? ctx->gev : ctx->ev;
+    std::vector<int>& kinds = ctx->capturing ? ctx->gev_kind : ctx->ev_kind;
+    size_t& used = ctx->capturing ? ctx->gev_used : ctx->ev_used;
+    if (used == ev.size()) {
         cudaEvent_t e;
         PT_CUDA(ctx, cudaEventCreate(&e));
-        ctx->ev.push_back(e);
-        ctx->ev_kind.push_back(0);
+        ev.push_back(e);
+        kinds.push_back(0);
     }
-    ctx->ev_kind[ctx->ev_used] = kind;
-    PT_CUDA(ctx, cudaEventRecord(ctx->ev[ctx->ev_used], st));
-    ctx->ev_used++;
+    kinds[used] = kind;
+    if (ctx->capturing)  // becomes an event-record node of the graph, recorded at every replay
+        PT_CUDA(ctx, cudaEventRecordWithFlags(ev[used], st, cudaEventRecordExternal));
+    else
+        PT_CUDA(ctx, cudaEventRecord(ev[used], st));
+    used++;
     return PT_OK;
 }
 
@@ -481,6 +494,7 @@ pt_status pt_destroy(pt_ctx* ctx) {
         if (t.sel_owned) cudaFree(t.sel_owned);
     }
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->gev) cudaEventDestroy(e);
     for (int p = 0; p < 2; ++p) {
         for (cudaEvent_t e : ctx->vev[p])
             if (e) cudaEventDestroy(e);
@@ -714,16 +728,22 @@ pt_status pt_run_transfer(pt_ctx* ctx) {
         return pt_run_backward(ctx);
     }
     if ((st = prepare_shapes(ctx)) != PT_OK) return st;
+    if (ctx->gexec && ctx->graph_timed != ctx->timing) {  // recapture with / without timing nodes
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
     if (!ctx->gexec) {
-        const bool timing = ctx->timing;
-        ctx->timing = false;  // no event records inside the captured graph
         const int64_t before = ctx->launches;
         PT_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        ctx->gev_used = 0;
         pt_status s0 = enqueue_pass(ctx, 0);
         pt_status s1 = s0 == PT_OK ? enqueue_pass(ctx, 1) : s0;
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-        ctx->timing = timing;
+        ctx->capturing = false;
+        ctx->graph_timed = ctx->timing;
+        ctx->graph_replays = 0;
         ctx->graph_kernels = ctx->launches - before;
         ctx->launches = before;
         if (s1 != PT_OK) {
@@ -738,9 +758,8 @@ pt_status pt_run_transfer(pt_ctx* ctx) {
             return fail(ctx, PT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
         }
     }
-    if ((st = record_event(ctx, 2, ctx->stream)) != PT_OK) return st;
     PT_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
-    if ((st = record_event(ctx, 2, ctx->stream)) != PT_OK) return st;
+    ctx->graph_replays++;
     ctx->launches += ctx->graph_kernels;
     ctx->passes_done = 3;
     return PT_OK;
@@ -846,6 +865,7 @@ pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on) {
     if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
     ctx->timing = on != 0;
     ctx->ev_used = 0;
+    ctx->graph_replays = 0;
     return PT_OK;
 }
 
@@ -855,12 +875,20 @@ pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launche
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     double t[3] = {0, 0, 0};
     int n[3] = {0, 0, 0};
-    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
-        float ms = 0.f;
-        PT_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
-        const int k = ctx->ev_kind[i];
-        t[k] += ms;
-        n[k] += 1;
+    auto sum = [&](const std::vector<cudaEvent_t>& ev, const std::vector<int>& kinds, size_t used) -> pt_status {
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float ms = 0.f;
+            PT_CUDA(ctx, cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            t[kinds[i]] += ms;
+            n[kinds[i]] += 1;
+        }
+        return PT_OK;
+    };
+    pt_status st = sum(ctx->ev, ctx->ev_kind, ctx->ev_used);
+    if (st != PT_OK) return st;
+    if (ctx->gexec && ctx->graph_timed && ctx->graph_replays > 0) {
+        st = sum(ctx->gev, ctx->gev_kind, ctx->gev_used);  // the most recent replay
+        if (st != PT_OK) return st;
     }
     if (scan_ms) *scan_ms = t[0];
     if (scan_launches) *scan_launches = n[0];

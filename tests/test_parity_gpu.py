@@ -167,3 +167,26 @@ def test_full_size_configs(oracle_lib, cfg):
     else:
         w = W.cyclic5()
     _check(w, oracle_lib)
+
+
+def test_kernel_timing_direct_and_graph():
+    """Scan kernels are bracketed by CUDA events in both launch modes."""
+    import paper_2307_15255_b300.pt as P
+    from _gpu import session_for
+    w = W.snowflake(scale=0.02)
+    s = session_for(w)
+    try:
+        P.pt_set_kernel_timing(s.ctx, True)
+        s.run()
+        kt = P.pt_get_kernel_time(s.ctx)
+        assert kt["scan_launches"] == 2 * w.n_tables and kt["scan_ms"] > 0
+        P.pt_set_graph_mode(s.ctx, True)
+        P.pt_set_kernel_timing(s.ctx, True)
+        n0 = P.pt_get_launch_count(s.ctx)
+        for _ in range(3):
+            s.run()
+        kt = P.pt_get_kernel_time(s.ctx)  # the last replay
+        assert kt["scan_launches"] == 2 * w.n_tables and kt["scan_ms"] > 0
+        assert P.pt_get_launch_count(s.ctx) - n0 == 3 * (P.pt_get_launch_count(s.ctx) - n0) // 3 > 0
+    finally:
+        s.close()
