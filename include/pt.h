@@ -219,6 +219,72 @@ pt_status pt_get_launch_count(pt_ctx* ctx, int64_t* launches);
 pt_status pt_plan_graph(int32_t n_tables, const int64_t* n_rows, int32_t n_edges, const pt_edge* edges,
                         int32_t* src_out, int32_t* dst_out, int32_t* order_out, int32_t* level_out);
 
+/* ---- serving: resident tables, continuous batching ------------------------
+ * A server keeps tables resident in device memory and runs many transfer
+ * queries over them.  A query names up to 6 table instances (one use of a
+ * resident table with its own selection bitmap; the same table may appear
+ * more than once, as an alias) and up to 8 equi-join edges between
+ * instances (pt_edge with t0/t1 = instance indexes, c0/c1 = column indexes
+ * of those instances' tables).  Its transfer is the forward and backward
+ * pass of Section 3.2 over its instances, with the filter specification
+ * above; the survivor bitmaps equal those of a planned context on the same
+ * tables, selections and edges.
+ *
+ * A scheduler thread admits waiting queries in arrival order while their
+ * device memory (bitmaps, filters, row ids, selection copies) fits the
+ * arena, groups up to max_batch of them and runs the group as one batch:
+ * per pass and per DAG level, one scan, one size/clear and one insert
+ * launch over the visits of every query in the batch, replayed from a CUDA
+ * graph.  Up to max_inflight (1..4) batches run at once; queries that
+ * arrive meanwhile join the next batch as soon as a slot and memory free
+ * up.  max_batch = max_inflight = 1 runs one query at a time.
+ *
+ * Resident key columns are each stored next to a column of their hashes,
+ * computed once by pt_server_start.  Results stay in device memory until
+ * pt_server_release.  Functions are thread-safe except that a ticket must
+ * not be released while another thread reads its survivors. */
+typedef struct pt_server pt_server;
+
+/* Create a server on the current device with an arena of arena_bytes of
+ * device memory for queries. */
+pt_status pt_server_create(pt_server** out, const pt_filter_cfg* cfg, int64_t arena_bytes, int32_t max_batch,
+                           int32_t max_inflight);
+
+/* Register a resident table (before pt_server_start).  Device columns are
+ * borrowed and must stay valid; host columns are copied. */
+pt_status pt_server_register_table(pt_server* srv, int64_t n_rows, int32_t n_cols, const pt_column* cols,
+                                   int32_t* table_id);
+
+/* Compute the hash columns, allocate the batch descriptors and start the
+ * scheduler.  Synchronous. */
+pt_status pt_server_start(pt_server* srv);
+
+/* Submit a query.  table_ids[i] is instance i's resident table; sel_bitmaps
+ * (nullable, or NULL entries) are host bitmaps, copied before returning. */
+pt_status pt_server_submit(pt_server* srv, int32_t n_inst, const int32_t* table_ids, const uint32_t* const* sel_bitmaps,
+                           int32_t n_edges, const pt_edge* edges, uint64_t* ticket);
+
+/* *done = 1 once the query finished; *result is its status. */
+pt_status pt_server_poll(pt_server* srv, uint64_t ticket, int32_t* done, pt_status* result);
+
+/* Block until the query finished. */
+pt_status pt_server_wait(pt_server* srv, uint64_t ticket, pt_status* result);
+
+/* Final (backward-pass) survivors of instance inst: bitmap into bitmap_out
+ * (host or device, nullable) and count into *count_out (nullable). */
+pt_status pt_server_survivors(pt_server* srv, uint64_t ticket, int32_t inst, uint32_t* bitmap_out, int64_t* count_out);
+
+/* Free a finished query's device memory and forget its ticket. */
+pt_status pt_server_release(pt_server* srv, uint64_t ticket);
+
+/* Latency percentiles (submit to completion) and throughput of the queries
+ * completed since creation or the last pt_server_reset_stats. */
+pt_status pt_server_stats(pt_server* srv, double* p50_ms, double* p99_ms, double* qps, int64_t* completed);
+pt_status pt_server_reset_stats(pt_server* srv);
+
+/* Stop the scheduler (after in-flight batches finish) and free everything. */
+pt_status pt_server_destroy(pt_server* srv);
+
 /* ---- one visit without any allocation ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: code running while a stream is being
@@ -273,9 +339,9 @@ pt_status pt_visit_static(const pt_filter_cfg* cfg, void* cuda_stream, int64_t n
                           int32_t n_in, const pt_static_probe* in, int32_t n_out, const pt_static_build* out,
                           uint32_t* out_bits, int64_t* count_out);
 
-/* Message of the last failed call on ctx (or of the last failed pt_create /
- * pt_plan_graph / pt_visit_static when ctx is NULL).  Valid until the next
- * call on ctx. */
+/* Message of the last failed call on ctx (or, when ctx is NULL, of the last
+ * failed call that has no context: pt_create, pt_plan_graph, pt_server_*,
+ * pt_visit_static).  Valid until the next call on ctx. */
 const char* pt_last_error(pt_ctx* ctx);
 
 #ifdef __cplusplus

@@ -29,11 +29,17 @@ __host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) {
     return (size_t)(scan_queue_words(n_in) + n_in * kRoundWords + kRoundWords) * 4;
 }
 
+constexpr int32_t kHashed = 2;  // column dtype: uint64 values that already are H(key)
+
 struct ColRef {
     const void* p;
-    int32_t dtype;  // 0 = int32, 1 = int64
+    int32_t dtype;  // 0 = int32, 1 = int64, kHashed = precomputed key hashes
     int32_t pad;
 };
+
+// Fill out[i] = H(key[i]) for a resident column (dtype 0 or 1).
+cudaError_t launch_hash_column(const void* keys, int32_t dtype, int64_t n, uint64_t seed, uint64_t* out,
+                               cudaStream_t s);
 
 // An incoming edge of a visit: the visit's key column(s) on the edge and
 // the filter the other end built earlier in the same pass.
@@ -86,11 +92,30 @@ struct VisitArgs {
     ColRef bcol[kMaxBuildCols];
 };
 
+// One task of a batched launch: part `part` of visit `visit` (an index into
+// the launch's VisitArgs array).  For scans, part is the CTA index in the
+// visit's grid; for size/clear and insert, one of the launch's `parts`.
+struct BatchTask {
+    int32_t visit;
+    int32_t part;
+};
+
 // Launchers (return the launch error, if any).
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
 cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+
+// Batched launches read their task range {first, count} from device memory
+// (range[0], range[1]) so that one captured graph serves every batch.
+cudaError_t launch_scan_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                              const FilterCfg& f, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_size_clear_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                                    int parts, const FilterCfg& f, int grid, int block, cudaStream_t s);
+cudaError_t launch_insert_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range, int parts,
+                                const FilterCfg& f, int grid, int block, cudaStream_t s);
+int scan_batch_max_ctas_per_sm(int block_bits, int block, size_t smem);
+cudaError_t scan_batch_set_smem_limit(int block_bits, size_t smem);
 
 // Message returned by pt_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);

@@ -31,21 +31,21 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 __device__ __forceinline__ uint64_t hash_key(uint64_t x, uint64_t seed) { return mix64((x ^ seed) + kGamma); }
 
-__device__ __forceinline__ uint64_t hash_pair(uint64_t a, uint64_t b, uint64_t seed) {
-    return mix64(hash_key(a, seed) ^ b);
-}
-
 // Key of row r as u64; int32 values are sign-extended.
 __device__ __forceinline__ uint64_t load_key(const ColRef& c, uint32_t r) {
     if (c.dtype == 0) return (uint64_t)(int64_t)__ldg(reinterpret_cast<const int32_t*>(c.p) + r);
     return (uint64_t)__ldg(reinterpret_cast<const long long*>(c.p) + r);
 }
 
+// Hash of row r's key on an edge.  A first column of dtype kHashed already
+// holds H(x) of its key (precomputed for resident tables), so only the
+// composite step, if any, is left.
 __device__ __forceinline__ uint64_t edge_hash(const ColRef& c0, const ColRef& c1, int ncols, uint32_t r,
                                               uint64_t seed) {
     const uint64_t a = load_key(c0, r);
-    if (ncols == 2) return hash_pair(a, load_key(c1, r), seed);
-    return hash_key(a, seed);
+    const uint64_t h = c0.dtype == kHashed ? a : hash_key(a, seed);
+    if (ncols == 2) return mix64(h ^ load_key(c1, r));
+    return h;
 }
 
 // 32-byte sectors of a column holding at least one set row of a 32-row
@@ -150,12 +150,21 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
 // survivor words are stored, and their row ids are compacted into the
 // warp's segment of the id array with ballot/popc ranks.
 // ---------------------------------------------------------------------------
+// Shared state of one scan CTA besides the dynamic filter/queue area.
+struct ScanShared {
+    ProbeEdge pe[kMaxIn];  // incoming edges in probe order
+    int32_t off[kMaxIn];   // word offset of the filter in smem, or -1: probe from global
+    uint32_t nb[kMaxIn];
+};
+
+// One CTA of a visit's scan: `cta` is its index in the visit's grid of
+// total_warps / (blockDim.x / 32) CTAs.  Every thread of the block calls it.
 template <int B, int KT>
-__global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ ProbeEdge s_pe[kMaxIn];     // incoming edges in probe order
-    __shared__ int32_t s_off[kMaxIn];      // word offset of the filter in smem, or -1: probe from global
-    __shared__ uint32_t s_nb[kMaxIn];
+__device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f, int64_t cta, uint32_t* smem,
+                                         ScanShared& sh) {
+    ProbeEdge* s_pe = sh.pe;
+    int32_t* s_off = sh.off;
+    uint32_t* s_nb = sh.nb;
     constexpr uint32_t WPB = B / 32;
     const uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);  // shared-window address of the filters
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
     uint32_t* abm = wsm + scan_queue_words(n_in);          // [n_in][kRoundWords] rows entering each stage
     uint32_t* obm = abm + n_in * kRoundWords;               // [kRoundWords] survivors of the round
 
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t gw = cta * (blockDim.x >> 5) + warp;
     const int64_t n_words = (a.n + 31) >> 5;
     const int64_t w_begin = gw * a.words_per_warp;
     const int64_t w_end = min(n_words, w_begin + a.words_per_warp);
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
                         else if (next_dense)
                             load8(sub_row0 + 1024u, kn);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) h[i] = hash_key(h[i], seed);
+                        for (int i = 0; i < 8; ++i) h[i] = d_col.dtype == kHashed ? h[i] : hash_key(h[i], seed);
                         bool pass[8];
                         if (off >= 0) {
 #pragma unroll
@@ -522,13 +531,50 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kerne
     }
 }
 
+template <int B, int KT>
+__global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ ScanShared sh;
+    scan_cta<B, KT>(a, f, blockIdx.x, smem, sh);
+}
+
+// Copy a visit's arguments from global memory into shared memory (all threads).
+__device__ __forceinline__ void load_visit(VisitArgs& dst, const VisitArgs* src) {
+    static_assert(sizeof(VisitArgs) % 8 == 0, "VisitArgs is copied in 8-byte words");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+    for (unsigned i = threadIdx.x; i < sizeof(VisitArgs) / 8; i += blockDim.x) d[i] = s[i];
+}
+
+// Batched scan: one launch runs the scans of many visits (of many queries);
+// task t is CTA tasks[t].part of visit tasks[t].visit.  Tasks of one launch
+// must not depend on each other.
+template <int B, int KT>
+__global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
+    pt_scan_batch_kernel(const VisitArgs* visits, const BatchTask* task_base, const int32_t* range, const FilterCfg f) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ ScanShared sh;
+    __shared__ __align__(16) VisitArgs s_a;
+    const BatchTask* tasks = task_base + range[0];
+    const int32_t n = range[1];
+    for (int32_t t = blockIdx.x; t < n; t += gridDim.x) {
+        const BatchTask task = tasks[t];
+        load_visit(s_a, visits + task.visit);
+        __syncthreads();
+        scan_cta<B, KT>(s_a, f, task.part, smem, sh);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 2. size + clear the outgoing filters from the device-side survivor count
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) pt_size_clear_kernel(const VisitArgs a, const FilterCfg f) {
+// Part `part` of `nparts` of a visit's size/clear (thread t of the part zeroes
+// every (nparts * blockDim)-th 16-byte chunk from (part * blockDim + t)).
+__device__ __forceinline__ void size_clear_part(const VisitArgs& a, const FilterCfg& f, int64_t part, int64_t nparts) {
     const unsigned long long c = *a.count;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = (size_t)part * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)nparts * blockDim.x;
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e) {
         if (e >= a.n_out) break;
@@ -542,21 +588,42 @@ __global__ void __launch_bounds__(512) pt_size_clear_kernel(const VisitArgs a, c
     }
 }
 
+__global__ void __launch_bounds__(512) pt_size_clear_kernel(const VisitArgs a, const FilterCfg f) {
+    size_clear_part(a, f, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(512)
+    pt_size_clear_batch_kernel(const VisitArgs* visits, const BatchTask* task_base, const int32_t* range,
+                               const int32_t parts, const FilterCfg f) {
+    __shared__ __align__(16) VisitArgs s_a;
+    const BatchTask* tasks = task_base + range[0];
+    const int32_t n = range[1];
+    for (int32_t t = blockIdx.x; t < n; t += gridDim.x) {
+        const BatchTask task = tasks[t];
+        load_visit(s_a, visits + task.visit);
+        __syncthreads();
+        size_clear_part(s_a, f, task.part, parts);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 3. insert the survivors' outgoing keys
 // ---------------------------------------------------------------------------
+// Part `part` of `nparts` of a visit's insert: warp w of the part takes the
+// segments s = part * warps + w, then every (nparts * warps)-th one.
 template <int B, int KT>
-__global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
+__device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg& f, int64_t part, int64_t nparts,
+                                            uint32_t* s_nb) {
     using BB = BlockBits<B>;
-    __shared__ uint32_t s_nb[kMaxOut];
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e)
         if (threadIdx.x == (unsigned)e && e < a.n_out) s_nb[e] = (uint32_t)*a.out[e].nblocks;
     __syncthreads();
 
     const uint32_t lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = part * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t n_warps = nparts * (blockDim.x >> 5);
     const size_t seg_rows = (size_t)a.words_per_warp * 32;
     const int k = f.k;
     const uint64_t seed = f.seed;
@@ -619,6 +686,29 @@ __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const
     }
 }
 
+template <int B, int KT>
+__global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
+    __shared__ uint32_t s_nb[kMaxOut];
+    insert_part<B, KT>(a, f, blockIdx.x, gridDim.x, s_nb);
+}
+
+template <int B, int KT>
+__global__ void __launch_bounds__(512)
+    pt_insert_batch_kernel(const VisitArgs* visits, const BatchTask* task_base, const int32_t* range,
+                           const int32_t parts, const FilterCfg f) {
+    __shared__ uint32_t s_nb[kMaxOut];
+    __shared__ __align__(16) VisitArgs s_a;
+    const BatchTask* tasks = task_base + range[0];
+    const int32_t n = range[1];
+    for (int32_t t = blockIdx.x; t < n; t += gridDim.x) {
+        const BatchTask task = tasks[t];
+        load_visit(s_a, visits + task.visit);
+        __syncthreads();
+        insert_part<B, KT>(s_a, f, task.part, parts, s_nb);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
@@ -671,6 +761,77 @@ cudaError_t scan_set_smem_limit(int block_bits, size_t smem) {
     }
     if ((e = cudaFuncSetAttribute(pt_scan_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(pt_scan_kernel<256, 0>, at, (int)smem);
+}
+
+cudaError_t launch_scan_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                              const FilterCfg& f, int grid, int block, size_t smem, cudaStream_t s) {
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_scan_batch_kernel<512, 4><<<grid, block, smem, s>>>(visits, tasks, range, f);
+        else pt_scan_batch_kernel<512, 0><<<grid, block, smem, s>>>(visits, tasks, range, f);
+    } else {
+        if (f.k == 4) pt_scan_batch_kernel<256, 4><<<grid, block, smem, s>>>(visits, tasks, range, f);
+        else pt_scan_batch_kernel<256, 0><<<grid, block, smem, s>>>(visits, tasks, range, f);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_size_clear_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                                    int parts, const FilterCfg& f, int grid, int block, cudaStream_t s) {
+    pt_size_clear_batch_kernel<<<grid, block, 0, s>>>(visits, tasks, range, parts, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range, int parts,
+                                const FilterCfg& f, int grid, int block, cudaStream_t s) {
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_insert_batch_kernel<512, 4><<<grid, block, 0, s>>>(visits, tasks, range, parts, f);
+        else pt_insert_batch_kernel<512, 0><<<grid, block, 0, s>>>(visits, tasks, range, parts, f);
+    } else {
+        if (f.k == 4) pt_insert_batch_kernel<256, 4><<<grid, block, 0, s>>>(visits, tasks, range, parts, f);
+        else pt_insert_batch_kernel<256, 0><<<grid, block, 0, s>>>(visits, tasks, range, parts, f);
+    }
+    return cudaGetLastError();
+}
+
+int scan_batch_max_ctas_per_sm(int block_bits, int block, size_t smem) {
+    int n = 0, m = 0;
+    if (block_bits == 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_batch_kernel<512, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_batch_kernel<512, 0>, block, smem);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_batch_kernel<256, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_batch_kernel<256, 0>, block, smem);
+    }
+    return n < m ? n : m;
+}
+
+cudaError_t scan_batch_set_smem_limit(int block_bits, size_t smem) {
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (block_bits == 512) {
+        if ((e = cudaFuncSetAttribute(pt_scan_batch_kernel<512, 4>, at, (int)smem)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(pt_scan_batch_kernel<512, 0>, at, (int)smem);
+    }
+    if ((e = cudaFuncSetAttribute(pt_scan_batch_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pt_scan_batch_kernel<256, 0>, at, (int)smem);
+}
+
+namespace {
+__global__ void pt_hash_column_kernel(const void* keys, int32_t dtype, int64_t n, uint64_t seed, uint64_t* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        ColRef c{keys, dtype, 0};
+        out[i] = hash_key(load_key(c, (uint32_t)i), seed);
+    }
+}
+}  // namespace
+
+cudaError_t launch_hash_column(const void* keys, int32_t dtype, int64_t n, uint64_t seed, uint64_t* out,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t grid = (n + 255) / 256;
+    if (grid > 148 * 32) grid = 148 * 32;
+    pt_hash_column_kernel<<<(int)grid, 256, 0, s>>>(keys, dtype, n, seed, out);
+    return cudaGetLastError();
 }
 
 }  // namespace pt

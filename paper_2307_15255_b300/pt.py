@@ -95,6 +95,19 @@ _SIGS = {
     "pt_last_error": (C.c_char_p, [_P]),
     "pt_visit_static": (C.c_int, [C.POINTER(pt_filter_cfg), _P, C.c_int64, _P, C.c_int32,
                                   C.POINTER(pt_static_probe), C.c_int32, C.POINTER(pt_static_build), _P, _P]),
+    "pt_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(pt_filter_cfg), C.c_int64, C.c_int32, C.c_int32]),
+    "pt_server_register_table": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(pt_column), C.POINTER(C.c_int32)]),
+    "pt_server_start": (C.c_int, [_P]),
+    "pt_server_submit": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int32,
+                                   C.POINTER(pt_edge), C.POINTER(C.c_uint64)]),
+    "pt_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int)]),
+    "pt_server_wait": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int)]),
+    "pt_server_survivors": (C.c_int, [_P, C.c_uint64, C.c_int32, _P, C.POINTER(C.c_int64)]),
+    "pt_server_release": (C.c_int, [_P, C.c_uint64]),
+    "pt_server_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_int64)]),
+    "pt_server_reset_stats": (C.c_int, [_P]),
+    "pt_server_destroy": (C.c_int, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -279,3 +292,73 @@ def pt_plan_graph(n_rows: Sequence[int], edges: Sequence[tuple]) -> dict:
     _check(lib.pt_plan_graph(nt, C.cast(nr, _P), ne, _edges(edges), C.cast(src, _P), C.cast(dst, _P),
                              C.cast(order, _P), C.cast(level, _P)), "pt_plan_graph", None)
     return {"src": list(src)[:ne], "dst": list(dst)[:ne], "order": list(order), "level": list(level)}
+
+
+# ---- serving ---------------------------------------------------------------
+
+def pt_server_create(bits_per_key: int = 10, k: int = 4, block_bits: int = 256, seed: int = 0,
+                     arena_bytes: int = 1 << 30, max_batch: int = 16, max_inflight: int = 2) -> int:
+    cfg = pt_filter_cfg(bits_per_key, k, block_bits, 0, seed)
+    out = _P()
+    _check(lib.pt_server_create(C.byref(out), C.byref(cfg), arena_bytes, max_batch, max_inflight),
+           "pt_server_create", None)
+    return out.value
+
+
+def pt_server_register_table(srv: int, n_rows: int, cols: Sequence[Tuple[int, int, int]]) -> int:
+    arr = _columns(cols)
+    tid = C.c_int32()
+    _check(lib.pt_server_register_table(srv, n_rows, len(cols), arr, C.byref(tid)), "pt_server_register_table", None)
+    return tid.value
+
+
+def pt_server_start(srv: int) -> None:
+    _check(lib.pt_server_start(srv), "pt_server_start", None)
+
+
+def pt_server_submit(srv: int, table_ids: Sequence[int], sel_ptrs: Sequence[Optional[int]],
+                     edges: Sequence[tuple]) -> int:
+    """sel_ptrs: host addresses of uint32 bitmaps (or None) per instance; copied before returning."""
+    n = len(table_ids)
+    ids = (C.c_int32 * n)(*table_ids)
+    sels = (_P * n)(*[p for p in sel_ptrs])
+    t = C.c_uint64()
+    _check(lib.pt_server_submit(srv, n, ids, sels, len(edges), _edges(edges), C.byref(t)), "pt_server_submit", None)
+    return t.value
+
+
+def pt_server_poll(srv: int, ticket: int) -> Tuple[bool, int]:
+    done, res = C.c_int32(), C.c_int()
+    _check(lib.pt_server_poll(srv, ticket, C.byref(done), C.byref(res)), "pt_server_poll", None)
+    return bool(done.value), res.value
+
+
+def pt_server_wait(srv: int, ticket: int) -> int:
+    res = C.c_int()
+    _check(lib.pt_server_wait(srv, ticket, C.byref(res)), "pt_server_wait", None)
+    return res.value
+
+
+def pt_server_survivors(srv: int, ticket: int, inst: int, bitmap_out: Optional[int]) -> int:
+    c = C.c_int64()
+    _check(lib.pt_server_survivors(srv, ticket, inst, bitmap_out, C.byref(c)), "pt_server_survivors", None)
+    return c.value
+
+
+def pt_server_release(srv: int, ticket: int) -> None:
+    _check(lib.pt_server_release(srv, ticket), "pt_server_release", None)
+
+
+def pt_server_stats(srv: int) -> dict:
+    p50, p99, qps = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    _check(lib.pt_server_stats(srv, C.byref(p50), C.byref(p99), C.byref(qps), C.byref(n)), "pt_server_stats", None)
+    return {"p50_ms": p50.value, "p99_ms": p99.value, "qps": qps.value, "completed": n.value}
+
+
+def pt_server_reset_stats(srv: int) -> None:
+    _check(lib.pt_server_reset_stats(srv), "pt_server_reset_stats", None)
+
+
+def pt_server_destroy(srv: int) -> None:
+    _check(lib.pt_server_destroy(srv), "pt_server_destroy", None)
