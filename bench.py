@@ -192,6 +192,94 @@ def reference_arm(args) -> None:
 
 
 # ---------------------------------------------------------------------------
+# serving: resident star, Poisson arrivals, batched server vs one at a time
+# ---------------------------------------------------------------------------
+def serving_bench(args) -> dict:
+    import threading
+
+    import torch
+
+    from paper_2307_15255_b300 import pt as P
+
+    t0 = time.perf_counter()
+    w = W.star(scale=args.serving_scale, bits_per_key=args.bpk)
+    pool = W.selection_pool(w, size=32)
+    n_q = args.serving_queries
+    qs = W.serving_queries(w, n_q, rate_qps=0, pool=pool)
+    gen_s = time.perf_counter() - t0
+    cols_dev = [[torch.from_numpy(c).cuda() for c in t.cols] for t in w.tables]
+    sels = [[None if x is None else np.ascontiguousarray(x, dtype=np.uint32) for x in q.sel] for q in qs]
+
+    def make(max_batch, inflight):
+        srv = P.pt_server_create(w.bits_per_key, w.k, w.block_bits, w.seed, args.serving_arena_gb << 30, max_batch,
+                                 inflight)
+        for t, cols in zip(w.tables, cols_dev):
+            P.pt_server_register_table(srv, t.n_rows, [(c.data_ptr(), P.PT_I64, P.PT_MEM_DEVICE) for c in cols])
+        P.pt_server_start(srv)
+        return srv
+
+    def run(srv, idx, arrivals):
+        """Submit queries idx at the given arrival offsets (s); wait for all; stats."""
+        P.pt_server_reset_stats(srv)
+        tickets = [None] * len(idx)
+        start = time.perf_counter()
+
+        def submitter():
+            for j, i in enumerate(idx):
+                delay = arrivals[j] - (time.perf_counter() - start)
+                if delay > 0:
+                    time.sleep(delay)
+                q = qs[i]
+                tickets[j] = P.pt_server_submit(srv, q.inst_table,
+                                                [None if x is None else x.ctypes.data for x in sels[i]],
+                                                [(e.t0, e.c0, e.t1, e.c1) for e in q.edges])
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        for t in tickets:
+            P.pt_server_wait(srv, t)
+        wall = time.perf_counter() - start
+        st = P.pt_server_stats(srv)
+        for t in tickets:
+            P.pt_server_release(srv, t)
+        return {"queries": len(idx), "achieved_qps": len(idx) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]}
+
+    rng = np.random.default_rng(20230728 + 44)
+    # one at a time: a closed backlog, each query alone on the GPU
+    srv1 = make(1, 1)
+    run(srv1, list(range(min(20, n_q))), [0.0] * min(20, n_q))  # warm-up
+    n1 = min(args.serving_single, n_q)
+    single = run(srv1, list(range(n1)), [0.0] * n1)
+    P.pt_server_destroy(srv1)
+    cap1 = single["achieved_qps"]
+    # batched server: the same queries at Poisson arrival rates relative to that capacity
+    srv = make(args.serving_batch, 2)
+    run(srv, list(range(min(64, n_q))), [0.0] * min(64, n_q))  # warm-up: graphs captured
+    sweep = []
+    for mult in (0.5, 1.0, 2.0, 4.0):
+        rate = mult * cap1
+        nq = min(n_q, max(200, int(rate * 2.0)))
+        arr = np.cumsum(rng.exponential(1.0 / rate, nq))
+        r = run(srv, list(range(nq)), list(arr))
+        r.update({"offered_qps": rate, "offered_x_single": mult})
+        sweep.append(r)
+    sat = run(srv, list(range(n_q)), [0.0] * n_q)  # all queries at once: the batched capacity
+    sat.update({"offered": "all at once"})
+    P.pt_server_destroy(srv)
+    del cols_dev
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"star: fact {w.tables[0].n_rows} rows x 4 int64 FKs, dims "
+                    f"{[t.n_rows for t in w.tables[1:]]}; {n_q} queries of 3-6 instances, selectivity 0.1-50%",
+        "one_at_a_time": single,
+        "batched_sweep": sweep,
+        "batched_saturated": sat,
+        "throughput_x_one_at_a_time": sat["achieved_qps"] / cap1,
+        "max_batch": args.serving_batch, "inflight": 2, "generation_s": gen_s,
+    }
+
+
+# ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
 def kernel_source_hash() -> str:
@@ -359,6 +447,11 @@ def ours(args) -> None:
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n_e2e}
 
     s.close()
+    del tables_dev
+    torch.cuda.empty_cache()
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_bench(args)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -396,6 +489,7 @@ def ours(args) -> None:
         "clocks": clk.summary(),
         "gpu_launches": launches,
         "scale_mode": "replicas" if world > 1 else "single",
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -416,6 +510,12 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-scale", type=float, default=1.0, help="star size (1 = fact 100M rows)")
+    ap.add_argument("--serving-queries", type=int, default=2000)
+    ap.add_argument("--serving-single", type=int, default=200, help="queries timed one at a time")
+    ap.add_argument("--serving-batch", type=int, default=32)
+    ap.add_argument("--serving-arena-gb", type=int, default=96)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -336,16 +336,41 @@ class Query:
     arrival_s: float = 0.0
 
 
+def selection_pool(w: Workload, size: int = 32, seed: int = BASE_SEED + 41, sel_lo: float = 0.001,
+                   sel_hi: float = 0.5) -> List[List[np.ndarray]]:
+    """Per dimension table of a star, `size` exact-count uniform selections
+    with log-uniform selectivities in [sel_lo, sel_hi].
+
+    Each is a random window of one seeded permutation of the table's rows,
+    so a pool costs one permutation per table instead of one per query.
+    """
+    rng = _rng(seed)
+    pools: List[List[np.ndarray]] = [[]]
+    for t in w.tables[1:]:
+        n = t.n_rows
+        perm = rng.permutation(n)
+        pool = []
+        for _ in range(size):
+            frac = math.exp(rng.uniform(math.log(sel_lo), math.log(sel_hi)))
+            k = int(math.floor(frac * n))
+            start = int(rng.integers(0, n))
+            rows = np.concatenate([perm[start:start + k], perm[:max(0, start + k - n)]])
+            pool.append(bitmap_from_rows(n, rows))
+        pools.append(pool)
+    return pools
+
+
 def serving_queries(w: Workload, n_queries: int, rate_qps: float, seed: int = BASE_SEED + 40,
                     min_inst: int = 3, max_inst: int = 6, sel_lo: float = 0.001,
-                    sel_hi: float = 0.5) -> List[Query]:
+                    sel_hi: float = 0.5, pool: Optional[List[List[np.ndarray]]] = None) -> List[Query]:
     """Poisson arrivals of random connected star subgraphs.
 
     Each query takes the fact instance plus 2-4 distinct dimension
     instances (3-5 instances); a 6-instance query adds a second instance
     (an alias) of one chosen dimension, joined on the same foreign key.
     Every dimension instance gets a log-uniform selectivity in
-    [sel_lo, sel_hi].
+    [sel_lo, sel_hi] (drawn from `pool`, see :func:`selection_pool`, when
+    one is given).
     """
     rng = _rng(seed)
     t = 0.0
@@ -364,8 +389,11 @@ def serving_queries(w: Workload, n_queries: int, rate_qps: float, seed: int = BA
         edges = []
         for j, d in enumerate(dims, start=1):
             m = w.tables[d].n_rows
-            frac = math.exp(rng.uniform(math.log(sel_lo), math.log(sel_hi)))
-            sel.append(selection(rng, m, frac))
+            if pool is not None:
+                sel.append(pool[d][int(rng.integers(0, len(pool[d])))])
+            else:
+                frac = math.exp(rng.uniform(math.log(sel_lo), math.log(sel_hi)))
+                sel.append(selection(rng, m, frac))
             edges.append(Edge(0, (int(d) - 1,), j, (0,)))
         out.append(Query(inst_table, sel, edges, t))
     return out
