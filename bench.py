@@ -235,13 +235,22 @@ def serving_bench(args) -> dict:
                                                 [(e.t0, e.c0, e.t1, e.c1) for e in q.edges])
         th = threading.Thread(target=submitter)
         th.start()
+        # results are released as soon as they are done (in submission order), so
+        # that admission can reuse their memory; a stuck query ends the run
+        deadline = time.perf_counter() + args.serving_timeout
+        for j in range(len(idx)):
+            while tickets[j] is None:
+                if time.perf_counter() > deadline:
+                    raise RuntimeError("serving run did not finish in time")
+                time.sleep(1e-4)
+            while not P.pt_server_poll(srv, tickets[j])[0]:
+                if time.perf_counter() > deadline:
+                    raise RuntimeError("serving run did not finish in time")
+                time.sleep(2e-5)
+            P.pt_server_release(srv, tickets[j])
         th.join()
-        for t in tickets:
-            P.pt_server_wait(srv, t)
         wall = time.perf_counter() - start
         st = P.pt_server_stats(srv)
-        for t in tickets:
-            P.pt_server_release(srv, t)
         return {"queries": len(idx), "achieved_qps": len(idx) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]}
 
     rng = np.random.default_rng(20230728 + 44)
@@ -516,6 +525,7 @@ def main() -> None:
     ap.add_argument("--serving-single", type=int, default=200, help="queries timed one at a time")
     ap.add_argument("--serving-batch", type=int, default=32)
     ap.add_argument("--serving-arena-gb", type=int, default=96)
+    ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds per serving run")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
