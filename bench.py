@@ -200,6 +200,7 @@ def serving_bench(args) -> dict:
     import torch
 
     from paper_2307_15255_b300 import pt as P
+    from paper_2307_15255_b300.session import TransferSession
 
     t0 = time.perf_counter()
     w = W.star(scale=args.serving_scale, bits_per_key=args.bpk)
@@ -208,7 +209,13 @@ def serving_bench(args) -> dict:
     qs = W.serving_queries(w, n_q, rate_qps=0, pool=pool)
     gen_s = time.perf_counter() - t0
     cols_dev = [[torch.from_numpy(c).cuda() for c in t.cols] for t in w.tables]
-    sels = [[None if x is None else np.ascontiguousarray(x, dtype=np.uint32) for x in q.sel] for q in qs]
+    # the selection pool lives on the device; queries borrow its bitmaps
+    pool_dev = {}
+    for d in range(1, len(pool)):
+        for b in pool[d]:
+            pool_dev[id(b)] = torch.from_numpy(np.ascontiguousarray(b).view(np.int32)).cuda()
+    sel_ptrs = [[None if x is None else pool_dev[id(x)].data_ptr() for x in q.sel] for q in qs]
+    edges = [[(e.t0, e.c0, e.t1, e.c1) for e in q.edges] for q in qs]
 
     def make(max_batch, inflight):
         srv = P.pt_server_create(w.bits_per_key, w.k, w.block_bits, w.seed, args.serving_arena_gb << 30, max_batch,
@@ -218,8 +225,19 @@ def serving_bench(args) -> dict:
         P.pt_server_start(srv)
         return srv
 
-    def run(srv, idx, arrivals):
-        """Submit queries idx at the given arrival offsets (s); wait for all; stats."""
+    def submit(srv, i):
+        return P.pt_server_submit(srv, qs[i].inst_table, sel_ptrs[i], edges[i], P.PT_MEM_DEVICE)
+
+    def wait_release(srv, t, deadline):
+        while not P.pt_server_poll(srv, t)[0]:
+            if time.perf_counter() > deadline:
+                raise RuntimeError("serving run did not finish in time")
+            time.sleep(2e-5)
+        P.pt_server_release(srv, t)
+
+    def run_open(srv, idx, arrivals):
+        """Submit queries idx at the given arrival offsets (s) from a client
+        thread; release results as they complete (in submission order)."""
         P.pt_server_reset_stats(srv)
         tickets = [None] * len(idx)
         start = time.perf_counter()
@@ -229,61 +247,85 @@ def serving_bench(args) -> dict:
                 delay = arrivals[j] - (time.perf_counter() - start)
                 if delay > 0:
                     time.sleep(delay)
-                q = qs[i]
-                tickets[j] = P.pt_server_submit(srv, q.inst_table,
-                                                [None if x is None else x.ctypes.data for x in sels[i]],
-                                                [(e.t0, e.c0, e.t1, e.c1) for e in q.edges])
+                tickets[j] = submit(srv, i)
         th = threading.Thread(target=submitter)
         th.start()
-        # results are released as soon as they are done (in submission order), so
-        # that admission can reuse their memory; a stuck query ends the run
         deadline = time.perf_counter() + args.serving_timeout
         for j in range(len(idx)):
             while tickets[j] is None:
                 if time.perf_counter() > deadline:
                     raise RuntimeError("serving run did not finish in time")
                 time.sleep(1e-4)
-            while not P.pt_server_poll(srv, tickets[j])[0]:
-                if time.perf_counter() > deadline:
-                    raise RuntimeError("serving run did not finish in time")
-                time.sleep(2e-5)
-            P.pt_server_release(srv, tickets[j])
+            wait_release(srv, tickets[j], deadline)
         th.join()
         wall = time.perf_counter() - start
         st = P.pt_server_stats(srv)
         return {"queries": len(idx), "achieved_qps": len(idx) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]}
 
-    rng = np.random.default_rng(20230728 + 44)
-    # one at a time: a closed backlog, each query alone on the GPU
+    # one at a time through the server (batch of one, one in flight): each
+    # query is submitted when the previous one is done
     srv1 = make(1, 1)
-    run(srv1, list(range(min(20, n_q))), [0.0] * min(20, n_q))  # warm-up
+    deadline = time.perf_counter() + args.serving_timeout
+    for i in range(min(20, n_q)):
+        wait_release(srv1, submit(srv1, i), deadline)
+    P.pt_server_reset_stats(srv1)
     n1 = min(args.serving_single, n_q)
-    single = run(srv1, list(range(n1)), [0.0] * n1)
+    start = time.perf_counter()
+    for i in range(n1):
+        wait_release(srv1, submit(srv1, i), deadline)
+    wall1 = time.perf_counter() - start
+    st1 = P.pt_server_stats(srv1)
     P.pt_server_destroy(srv1)
+    single = {"queries": n1, "achieved_qps": n1 / wall1, "p50_ms": st1["p50_ms"], "p99_ms": st1["p99_ms"]}
     cap1 = single["achieved_qps"]
-    # batched server: the same queries at Poisson arrival rates relative to that capacity
+
+    # the plain path, one query at a time: a context per query (plan, run,
+    # read the survivors, free), keys hashed by the scan as in a single transfer
+    n_plain = min(args.serving_plain, n_q)
+    lat = []
+    for i in range(n_plain + 3):
+        q = qs[i]
+        t1 = time.perf_counter()
+        tabs = [(w.tables[t].n_rows, cols_dev[t], None if q.sel[j] is None else pool_dev[id(q.sel[j])])
+                for j, t in enumerate(q.inst_table)]
+        with TransferSession(tabs, edges[i], w.bits_per_key, w.k, w.block_bits, w.seed) as ts:
+            ts.run()
+            for j in range(len(tabs)):
+                ts.survivors(j)
+        if i >= 3:
+            lat.append(time.perf_counter() - t1)
+    lat.sort()
+    plain = {"queries": n_plain, "achieved_qps": n_plain / sum(lat), "p50_ms": lat[len(lat) // 2] * 1e3,
+             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3}
+
+    # batched server: the same queries at Poisson arrival rates relative to the
+    # one-at-a-time capacity, then all at once
+    rng = np.random.default_rng(20230728 + 44)
     srv = make(args.serving_batch, 2)
-    run(srv, list(range(min(64, n_q))), [0.0] * min(64, n_q))  # warm-up: graphs captured
+    run_open(srv, list(range(min(64, n_q))), [0.0] * min(64, n_q))  # warm-up: graphs captured
     sweep = []
-    for mult in (0.5, 1.0, 2.0, 4.0):
+    for mult in (0.5, 1.0, 2.0, 4.0, 8.0):
         rate = mult * cap1
-        nq = min(n_q, max(200, int(rate * 2.0)))
+        nq = min(n_q, max(200, int(rate * 1.0)))
         arr = np.cumsum(rng.exponential(1.0 / rate, nq))
-        r = run(srv, list(range(nq)), list(arr))
+        r = run_open(srv, list(range(nq)), list(arr))
         r.update({"offered_qps": rate, "offered_x_single": mult})
         sweep.append(r)
-    sat = run(srv, list(range(n_q)), [0.0] * n_q)  # all queries at once: the batched capacity
+    sat = run_open(srv, list(range(n_q)), [0.0] * n_q)
     sat.update({"offered": "all at once"})
     P.pt_server_destroy(srv)
-    del cols_dev
+    del cols_dev, pool_dev
     torch.cuda.empty_cache()
     return {
         "workload": f"star: fact {w.tables[0].n_rows} rows x 4 int64 FKs, dims "
-                    f"{[t.n_rows for t in w.tables[1:]]}; {n_q} queries of 3-6 instances, selectivity 0.1-50%",
+                    f"{[t.n_rows for t in w.tables[1:]]}; {n_q} queries of 3-6 instances, selectivity 0.1-50% "
+                    f"(seeded pool of 32 selections per dimension, device-resident)",
         "one_at_a_time": single,
+        "plain_context_one_at_a_time": plain,
         "batched_sweep": sweep,
         "batched_saturated": sat,
         "throughput_x_one_at_a_time": sat["achieved_qps"] / cap1,
+        "throughput_x_plain_context": sat["achieved_qps"] / plain["achieved_qps"],
         "max_batch": args.serving_batch, "inflight": 2, "generation_s": gen_s,
     }
 
@@ -523,6 +565,7 @@ def main() -> None:
     ap.add_argument("--serving-scale", type=float, default=1.0, help="star size (1 = fact 100M rows)")
     ap.add_argument("--serving-queries", type=int, default=2000)
     ap.add_argument("--serving-single", type=int, default=200, help="queries timed one at a time")
+    ap.add_argument("--serving-plain", type=int, default=30, help="queries timed through plain contexts")
     ap.add_argument("--serving-batch", type=int, default=32)
     ap.add_argument("--serving-arena-gb", type=int, default=96)
     ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds per serving run")

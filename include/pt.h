@@ -259,10 +259,12 @@ pt_status pt_server_register_table(pt_server* srv, int64_t n_rows, int32_t n_col
  * scheduler.  Synchronous. */
 pt_status pt_server_start(pt_server* srv);
 
-/* Submit a query.  table_ids[i] is instance i's resident table; sel_bitmaps
- * (nullable, or NULL entries) are host bitmaps, copied before returning. */
+/* Submit a query.  table_ids[i] is instance i's resident table;
+ * sel_bitmaps (nullable, or NULL entries = every row) are selection bitmaps
+ * in memory sel_mem: host bitmaps are copied before returning, device
+ * bitmaps (16-byte aligned) are borrowed until the query is done. */
 pt_status pt_server_submit(pt_server* srv, int32_t n_inst, const int32_t* table_ids, const uint32_t* const* sel_bitmaps,
-                           int32_t n_edges, const pt_edge* edges, uint64_t* ticket);
+                           int32_t sel_mem, int32_t n_edges, const pt_edge* edges, uint64_t* ticket);
 
 /* *done = 1 once the query finished; *result is its status. */
 pt_status pt_server_poll(pt_server* srv, uint64_t ticket, int32_t* done, pt_status* result);

@@ -126,7 +126,8 @@ struct Query {
     uint64_t ticket = 0;
     int n_inst = 0;
     int table[kMaxInst] = {};
-    std::vector<uint32_t> sel[kMaxInst];  // host copies of the selections (empty = every row)
+    std::vector<uint32_t> sel[kMaxInst];  // host copies of the selections (empty = none or borrowed)
+    const uint32_t* sel_dev[kMaxInst] = {};  // borrowed device selections
     int n_edges = 0;
     pt_edge edges[kMaxQEdges] = {};
     int32_t src[kMaxQEdges] = {}, dst[kMaxQEdges] = {};
@@ -330,7 +331,7 @@ void fill_args(pt_server* S, const Query* q, int p, const QVisit& vis, unsigned 
     int64_t* nblocks = (int64_t*)(counts + 3 * kMaxInst);
     a.n = S->tables[q->table[v]].n;
     if (p == 0)
-        a.in_bits = q->sel[v].empty() ? nullptr : (const uint32_t*)(base + q->o_sel[v]);
+        a.in_bits = q->sel_dev[v] ? q->sel_dev[v] : q->sel[v].empty() ? nullptr : (const uint32_t*)(base + q->o_sel[v]);
     else
         a.in_bits = (const uint32_t*)(base + q->o_surv[0][v]);
     a.out_bits = (uint32_t*)(base + q->o_surv[p][v]);
@@ -709,10 +710,11 @@ pt_status pt_server_start(pt_server* S) {
 }
 
 pt_status pt_server_submit(pt_server* S, int32_t n_inst, const int32_t* table_ids, const uint32_t* const* sel_bitmaps,
-                           int32_t n_edges, const pt_edge* edges, uint64_t* ticket) {
+                           int32_t sel_mem, int32_t n_edges, const pt_edge* edges, uint64_t* ticket) {
     if (!S || !table_ids || !ticket) return fail(PT_ERR_INVALID, "NULL argument");
     if (!S->started) return fail(PT_ERR_STATE, "pt_server_start has not run");
     if (n_inst < 1 || n_inst > kMaxInst) return fail(PT_ERR_INVALID, "n_inst %d (1..%d)", n_inst, kMaxInst);
+    if (sel_mem != PT_MEM_HOST && sel_mem != PT_MEM_DEVICE) return fail(PT_ERR_INVALID, "sel_mem %d", sel_mem);
     if (n_edges < 0 || n_edges > kMaxQEdges || (n_edges > 0 && !edges)) return fail(PT_ERR_INVALID, "n_edges %d", n_edges);
     std::unique_ptr<Query> q(new Query());
     q->n_inst = n_inst;
@@ -720,9 +722,14 @@ pt_status pt_server_submit(pt_server* S, int32_t n_inst, const int32_t* table_id
         if (table_ids[v] < 0 || table_ids[v] >= (int)S->tables.size()) return fail(PT_ERR_INVALID, "table id %d", table_ids[v]);
         q->table[v] = table_ids[v];
         if (sel_bitmaps && sel_bitmaps[v]) {
-            const size_t w = (size_t)((S->tables[table_ids[v]].n + 31) / 32);
-            q->sel[v].assign(sel_bitmaps[v], sel_bitmaps[v] + w);
-            if (w == 0) q->sel[v].push_back(0);
+            if (sel_mem == PT_MEM_DEVICE) {
+                if ((uintptr_t)sel_bitmaps[v] % 16) return fail(PT_ERR_INVALID, "device selection %d not 16-byte aligned", v);
+                q->sel_dev[v] = sel_bitmaps[v];
+            } else {
+                const size_t w = (size_t)((S->tables[table_ids[v]].n + 31) / 32);
+                q->sel[v].assign(sel_bitmaps[v], sel_bitmaps[v] + w);
+                if (w == 0) q->sel[v].push_back(0);
+            }
         }
     }
     for (int e = 0; e < n_edges; ++e) {

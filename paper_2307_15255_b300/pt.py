@@ -98,7 +98,7 @@ _SIGS = {
     "pt_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(pt_filter_cfg), C.c_int64, C.c_int32, C.c_int32]),
     "pt_server_register_table": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(pt_column), C.POINTER(C.c_int32)]),
     "pt_server_start": (C.c_int, [_P]),
-    "pt_server_submit": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int32,
+    "pt_server_submit": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int32, C.c_int32,
                                    C.POINTER(pt_edge), C.POINTER(C.c_uint64)]),
     "pt_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int)]),
     "pt_server_wait": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int)]),
@@ -317,13 +317,15 @@ def pt_server_start(srv: int) -> None:
 
 
 def pt_server_submit(srv: int, table_ids: Sequence[int], sel_ptrs: Sequence[Optional[int]],
-                     edges: Sequence[tuple]) -> int:
-    """sel_ptrs: host addresses of uint32 bitmaps (or None) per instance; copied before returning."""
+                     edges: Sequence[tuple], sel_mem: int = PT_MEM_HOST) -> int:
+    """sel_ptrs: addresses of uint32 bitmaps (or None) per instance: host memory
+    (copied before returning) or device memory (borrowed until done)."""
     n = len(table_ids)
     ids = (C.c_int32 * n)(*table_ids)
     sels = (_P * n)(*[p for p in sel_ptrs])
     t = C.c_uint64()
-    _check(lib.pt_server_submit(srv, n, ids, sels, len(edges), _edges(edges), C.byref(t)), "pt_server_submit", None)
+    _check(lib.pt_server_submit(srv, n, ids, sels, sel_mem, len(edges), _edges(edges), C.byref(t)),
+           "pt_server_submit", None)
     return t.value
 
 

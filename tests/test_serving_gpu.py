@@ -28,7 +28,7 @@ def query_workload(w, q):
     return W.Workload("q", tables, q.edges, w.bits_per_key, w.k, w.block_bits, w.seed)
 
 
-def run_server(w, qs, max_batch, max_inflight, arena):
+def run_server(w, qs, max_batch, max_inflight, arena, device_sel=False):
     import paper_2307_15255_b300.pt as P
     srv = P.pt_server_create(w.bits_per_key, w.k, w.block_bits, w.seed, arena, max_batch, max_inflight)
     keep = []
@@ -40,10 +40,18 @@ def run_server(w, qs, max_batch, max_inflight, arena):
         P.pt_server_start(srv)
         tickets = []
         for q in qs:
-            sels = [None if s is None else np.ascontiguousarray(s, dtype=np.uint32) for s in q.sel]
+            if device_sel:
+                sels = [None if s is None else torch.from_numpy(np.ascontiguousarray(s).view(np.int32)).cuda()
+                        for s in q.sel]
+                ptrs = [None if s is None else s.data_ptr() for s in sels]
+                mem = P.PT_MEM_DEVICE
+            else:
+                sels = [None if s is None else np.ascontiguousarray(s, dtype=np.uint32) for s in q.sel]
+                ptrs = [None if s is None else s.ctypes.data for s in sels]
+                mem = P.PT_MEM_HOST
             keep += [s for s in sels if s is not None]
-            tickets.append(P.pt_server_submit(srv, q.inst_table, [None if s is None else s.ctypes.data for s in sels],
-                                              [(e.t0, e.c0, e.t1, e.c1) for e in q.edges]))
+            tickets.append(P.pt_server_submit(srv, q.inst_table, ptrs, [(e.t0, e.c0, e.t1, e.c1) for e in q.edges],
+                                              mem))
         out = []
         for q, t in zip(qs, tickets):
             assert P.pt_server_wait(srv, t) == P.PT_OK
@@ -62,10 +70,11 @@ def run_server(w, qs, max_batch, max_inflight, arena):
         P.pt_server_destroy(srv)
 
 
-@pytest.mark.parametrize("max_batch,max_inflight,arena", [(8, 2, 1 << 30), (1, 1, 1 << 30), (4, 2, 60 << 20)])
-def test_served_results_equal_oracle(star, oracle_lib, max_batch, max_inflight, arena):
+@pytest.mark.parametrize("max_batch,max_inflight,arena,device_sel", [(8, 2, 1 << 30, False), (1, 1, 1 << 30, False),
+                                                                    (4, 2, 60 << 20, False), (16, 3, 1 << 30, True)])
+def test_served_results_equal_oracle(star, oracle_lib, max_batch, max_inflight, arena, device_sel):
     w, qs = star
-    got = run_server(w, qs, max_batch, max_inflight, arena)
+    got = run_server(w, qs, max_batch, max_inflight, arena, device_sel)
     for q, res in zip(qs, got):
         want = oracle_lib.transfer(query_workload(w, q))
         for j, (bm, c) in enumerate(res):
