@@ -195,6 +195,12 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
  * at the next run; invalidates a captured graph. */
 pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes, int32_t ctas_per_sm);
 
+/* Thread-block clusters of the scan: an incoming filter too large for one
+ * CTA's shared-memory budget is spread over the CTAs of a cluster (block j
+ * held by CTA j mod C) and probed through distributed shared memory.
+ * max_cluster is 1 (off), 2 or 4 (default).  Takes effect at the next run. */
+pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
+
 /* Kernel timing.  pt_set_kernel_timing(ctx, 1) records CUDA events around
  * every scan (probe + compact) launch and around every visit's size/clear +
  * insert pair, on the stream each runs on.  Direct launches accumulate

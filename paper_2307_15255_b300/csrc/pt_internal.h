@@ -87,6 +87,8 @@ struct VisitArgs {
     int32_t words_per_warp;          // bitmap words per scan warp; segment s starts at row s*32*wpw
     int32_t smem_words;              // shared-memory filter budget of one CTA (uint32 words)
     int32_t total_warps;             // scan warps launched (= segments)
+    int32_t cluster;                 // CTAs per thread-block cluster of the scan (1, 2 or 4)
+    int32_t pad_;
     ProbeEdge in[kMaxIn];
     BuildEdge out[kMaxOut];
     ColRef bcol[kMaxBuildCols];
@@ -109,7 +111,7 @@ cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int 
 // Batched launches read their task range {first, count} from device memory
 // (range[0], range[1]) so that one captured graph serves every batch.
 cudaError_t launch_scan_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
-                              const FilterCfg& f, int grid, int block, size_t smem, cudaStream_t s);
+                              const FilterCfg& f, int cluster, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_size_clear_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
                                     int parts, const FilterCfg& f, int grid, int block, cudaStream_t s);
 cudaError_t launch_insert_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range, int parts,

@@ -14,6 +14,8 @@
 //      blocks it will use.
 //   3. pt_insert_kernel  -- walks the compacted ids, gathers the outgoing
 //      key(s), hashes them and sets k bits with word-level atomicOr.
+#include <cooperative_groups.h>
+
 #include "pt_internal.h"
 
 namespace pt {
@@ -91,6 +93,24 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
     return v;
 }
 
+// Address in CTA `rank` of this cluster of the shared-memory location at
+// (this CTA's) shared-window address `addr`, and a load through it.
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(addr), "r"(rank));
+    return d;
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 template <int B>
 struct BlockBits {
     static constexpr uint32_t LOGB = B == 256 ? 8 : 9;
@@ -135,6 +155,27 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
     return ok & 1u;
 }
 
+// Probe a filter spread over the CTAs of a cluster of 2^lc CTAs: block j is
+// block j >> lc of the part held by CTA j & (2^lc - 1), at byte address
+// sbase in every CTA's shared window.
+template <int B, int KT>
+__device__ __forceinline__ bool probe_cluster(uint32_t sbase, uint32_t lc, uint32_t nb, uint64_t h, int k) {
+    using BB = BlockBits<B>;
+    const uint32_t lo = (uint32_t)h;
+    const uint32_t j = mul_hi((uint32_t)(h >> 32), nb);
+    const uint32_t blk = mapa_u32(mad_lo(j >> lc, B / 8, sbase), j & ((1u << lc) - 1u));
+    const uint32_t h2 = (lo >> 16) | 1u;
+    const int kk = KT > 0 ? KT : k;
+    uint32_t ok = 0xFFFFFFFFu;
+#pragma unroll 4
+    for (int i = 0; i < kk; ++i) {
+        const uint32_t ai = mad_lo((uint32_t)i, h2, lo);
+        const uint32_t wi = mul_hi(mad_lo(ai, BB::SCALE, 0u), BB::WPB);
+        ok &= rot_r(ld_cluster_u32(mad_lo(wi, 4u, blk)), ai);
+    }
+    return ok & 1u;
+}
+
 // ---------------------------------------------------------------------------
 // 1. scan: probe every incoming filter, write the survivor bitmap, compact
 //
@@ -155,16 +196,20 @@ struct ScanShared {
     ProbeEdge pe[kMaxIn];  // incoming edges in probe order
     int32_t off[kMaxIn];   // word offset of the filter in smem, or -1: probe from global
     uint32_t nb[kMaxIn];
+    uint32_t split[kMaxIn];  // 1: the filter is spread over the cluster (this CTA holds its part)
 };
 
 // One CTA of a visit's scan: `cta` is its index in the visit's grid of
 // total_warps / (blockDim.x / 32) CTAs.  Every thread of the block calls it.
 template <int B, int KT>
-__device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f, int64_t cta, uint32_t* smem,
-                                         ScanShared& sh) {
+__device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f, int64_t cta, uint32_t crank,
+                                         uint32_t* smem, ScanShared& sh) {
     ProbeEdge* s_pe = sh.pe;
     int32_t* s_off = sh.off;
     uint32_t* s_nb = sh.nb;
+    uint32_t* s_split = sh.split;
+    const uint32_t C = a.cluster > 1 ? (uint32_t)a.cluster : 1u;
+    const uint32_t lc = __ffs(C) - 1;  // C is 1, 2 or 4
     constexpr uint32_t WPB = B / 32;
     const uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);  // shared-window address of the filters
@@ -194,17 +239,26 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
             }
             ord[j + 1] = x;
         }
-        // Shared-memory placement, greedily in probe order.
+        // Shared-memory placement, greedily in probe order: a whole copy in
+        // every CTA when it fits, else (in a cluster) 1/C of it in each CTA of
+        // the cluster, else probed from global memory.  Every CTA of a cluster
+        // computes the same placement from the same counts.
         int32_t used = 0;
         for (int i = 0; i < a.n_in; ++i) {
             const ProbeEdge& pe = a.in[ord[i]];
             s_pe[i] = pe;
             const uint32_t nb = (uint32_t)*pe.nblocks;
             s_nb[i] = nb;
+            s_split[i] = 0;
             const int64_t words = (int64_t)nb * WPB;
+            const int64_t part = (int64_t)((nb + C - 1) >> lc) * WPB;
             if (used + words <= a.smem_words) {
                 s_off[i] = used;
                 used += (int32_t)words;
+            } else if (C > 1 && used + part <= a.smem_words) {
+                s_off[i] = used;
+                s_split[i] = 1;
+                used += (int32_t)part;
             } else {
                 s_off[i] = -1;
             }
@@ -216,10 +270,20 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         if (s_off[i] < 0) continue;
         const uint4* src = reinterpret_cast<const uint4*>(s_pe[i].filter);
         uint4* dst = reinterpret_cast<uint4*>(smem + s_off[i]);
-        const uint32_t n16 = s_nb[i] * (WPB / 4);
-        for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
+        if (!s_split[i]) {
+            const uint32_t n16 = s_nb[i] * (WPB / 4);
+            for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
+        } else {
+            // this CTA's part: blocks crank, crank + C, crank + 2C, ...
+            const uint32_t nl = (s_nb[i] + C - 1 - crank) >> lc;
+            for (uint32_t t = threadIdx.x; t < nl * (WPB / 4); t += blockDim.x) {
+                const uint32_t l = t / (WPB / 4), piece = t % (WPB / 4);
+                dst[t] = __ldg(src + (size_t)((l << lc) + crank) * (WPB / 4) + piece);
+            }
+        }
     }
     __syncthreads();
+    if (C > 1) cooperative_groups::this_cluster().sync();  // every part in place before any probe
 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -255,6 +319,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         const int ncols = s_pe[s].ncols;
         const int32_t off = s_off[s];
         const uint32_t nb = s_nb[s];
+        const uint32_t split = s_split[s];
         const uint32_t* fg = s_pe[s].filter;
         const bool last = s == n_in - 1;
         uint32_t* nq = queue + qoff(s + 1);
@@ -279,9 +344,12 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
 #pragma unroll
             for (int i = 0; i < R; ++i) h[i] = edge_hash(c0, c1, ncols, r[i], seed);
             bool pass[R];
-            if (off >= 0) {
+            if (off >= 0 && !split) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+            } else if (off >= 0) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) pass[i] = probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h[i], k);
             } else {
 #pragma unroll
                 for (int i = 0; i < R; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
@@ -313,8 +381,9 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                 bool pass = false;
                 if (live) {
                     const uint64_t h = edge_hash(c0, c1, ncols, r, seed);
-                    pass = off >= 0 ? probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h, k)
-                                    : probe_global<B, KT>(fg, nb, h, k);
+                    pass = off < 0   ? probe_global<B, KT>(fg, nb, h, k)
+                           : split ? probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h, k)
+                                   : probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h, k);
                 }
                 emit(pass, r);
             }
@@ -419,9 +488,12 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
 #pragma unroll
                         for (int i = 0; i < 8; ++i) h[i] = d_col.dtype == kHashed ? h[i] : hash_key(h[i], seed);
                         bool pass[8];
-                        if (off >= 0) {
+                        if (off >= 0 && !s_split[0]) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+                        } else if (off >= 0) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) pass[i] = probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h[i], k);
                         } else {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
@@ -529,13 +601,15 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         if (psec) atomicAdd(a.stats + 0, psec);
         if (bsec) atomicAdd(a.stats + 1, bsec);
     }
+    // no CTA of a cluster leaves (or reuses its shared memory) while another may still read its part
+    if (C > 1) cooperative_groups::this_cluster().sync();
 }
 
 template <int B, int KT>
 __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ScanShared sh;
-    scan_cta<B, KT>(a, f, blockIdx.x, smem, sh);
+    scan_cta<B, KT>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
 }
 
 // Copy a visit's arguments from global memory into shared memory (all threads).
@@ -557,11 +631,21 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
     __shared__ __align__(16) VisitArgs s_a;
     const BatchTask* tasks = task_base + range[0];
     const int32_t n = range[1];
-    for (int32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    // tasks are per cluster (the CTAs of a cluster share the task's filters);
+    // without clusters a cluster is one CTA
+    uint32_t C = 1, rank = 0;
+    {
+        const unsigned int cs = cooperative_groups::this_cluster().num_blocks();
+        if (cs > 1) {
+            C = cs;
+            rank = cluster_rank();
+        }
+    }
+    for (int32_t t = blockIdx.x / C; t < n; t += gridDim.x / C) {
         const BatchTask task = tasks[t];
         load_visit(s_a, visits + task.visit);
         __syncthreads();
-        scan_cta<B, KT>(s_a, f, task.part, smem, sh);
+        scan_cta<B, KT>(s_a, f, (int64_t)task.part * C + rank, rank, smem, sh);
         __syncthreads();
     }
 }
@@ -711,16 +795,39 @@ __global__ void __launch_bounds__(512)
 
 }  // namespace
 
+namespace {
+template <typename K, typename... Args>
+cudaError_t launch_maybe_cluster(K kernel, int cluster, int grid, int block, size_t smem, cudaStream_t s,
+                                 Args... args) {
+    if (cluster <= 1) {
+        kernel<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+}  // namespace
+
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s) {
+    const int c = a.cluster;
     if (f.block_bits == 512) {
-        if (f.k == 4) pt_scan_kernel<512, 4><<<grid, block, smem, s>>>(a, f);
-        else pt_scan_kernel<512, 0><<<grid, block, smem, s>>>(a, f);
-    } else {
-        if (f.k == 4) pt_scan_kernel<256, 4><<<grid, block, smem, s>>>(a, f);
-        else pt_scan_kernel<256, 0><<<grid, block, smem, s>>>(a, f);
+        if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<512, 4>, c, grid, block, smem, s, a, f);
+        return launch_maybe_cluster(pt_scan_kernel<512, 0>, c, grid, block, smem, s, a, f);
     }
-    return cudaGetLastError();
+    if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<256, 4>, c, grid, block, smem, s, a, f);
+    return launch_maybe_cluster(pt_scan_kernel<256, 0>, c, grid, block, smem, s, a, f);
 }
 
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s) {
@@ -764,15 +871,13 @@ cudaError_t scan_set_smem_limit(int block_bits, size_t smem) {
 }
 
 cudaError_t launch_scan_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
-                              const FilterCfg& f, int grid, int block, size_t smem, cudaStream_t s) {
+                              const FilterCfg& f, int cluster, int grid, int block, size_t smem, cudaStream_t s) {
     if (f.block_bits == 512) {
-        if (f.k == 4) pt_scan_batch_kernel<512, 4><<<grid, block, smem, s>>>(visits, tasks, range, f);
-        else pt_scan_batch_kernel<512, 0><<<grid, block, smem, s>>>(visits, tasks, range, f);
-    } else {
-        if (f.k == 4) pt_scan_batch_kernel<256, 4><<<grid, block, smem, s>>>(visits, tasks, range, f);
-        else pt_scan_batch_kernel<256, 0><<<grid, block, smem, s>>>(visits, tasks, range, f);
+        if (f.k == 4) return launch_maybe_cluster(pt_scan_batch_kernel<512, 4>, cluster, grid, block, smem, s, visits, tasks, range, f);
+        return launch_maybe_cluster(pt_scan_batch_kernel<512, 0>, cluster, grid, block, smem, s, visits, tasks, range, f);
     }
-    return cudaGetLastError();
+    if (f.k == 4) return launch_maybe_cluster(pt_scan_batch_kernel<256, 4>, cluster, grid, block, smem, s, visits, tasks, range, f);
+    return launch_maybe_cluster(pt_scan_batch_kernel<256, 0>, cluster, grid, block, smem, s, visits, tasks, range, f);
 }
 
 cudaError_t launch_size_clear_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,

@@ -44,6 +44,7 @@ struct Table {
 // Launch shape of one visit's scan.
 struct ScanShape {
     int grid = 1, block = 256;
+    int cluster = 1;         // CTAs per cluster (filters too large for one CTA spread over the cluster)
     size_t smem = 0;         // dynamic shared memory: filters + per-warp queues
     size_t filter_smem = 0;  // the filters' part
     int words_per_warp = 4, total_warps = 8;
@@ -53,7 +54,8 @@ struct Visit {
     int table = 0;
     std::vector<int> in_edges, out_edges;
     std::vector<int> bcols;  // distinct build columns
-    int64_t max_in_filter_bytes = 0;
+    int64_t max_in_filter_bytes = 0;     // sum over incoming edges of the filters' largest sizes
+    int64_t max_single_filter_bytes = 0; // the largest of them
     ScanShape shape;
 };
 
@@ -88,7 +90,8 @@ struct pt_ctx {
     int64_t seg_cap = 0;
 
     int scan_threads = 256;
-    int smem_budget = 40 * 1024;
+    int smem_budget = 96 * 1024;
+    int max_cluster = 4;  // 1: no clusters
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
     bool shapes_ready = false;
@@ -266,23 +269,35 @@ pt_status check_columns(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_co
     return PT_OK;
 }
 
+// Shared memory one scan CTA may use when two share an SM (228 KB per SM,
+// minus the kernel's static part).
+constexpr int64_t kScanCtaSmem = 112 * 1024;
+constexpr int kMaxCluster = 4;
+
 ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
     ScanShape s{};
     const int64_t n = ctx->tables[vis.table].n;
     const int64_t n_words = (n + 31) / 32;
     s.block = ctx->scan_threads;
     const int warps_per_cta = s.block / 32;
-    const int64_t want_filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
+    const size_t queues = (size_t)warps_per_cta * pt::scan_warp_smem_bytes((int)vis.in_edges.size());
+    int64_t budget = std::min<int64_t>(ctx->smem_budget, kScanCtaSmem - (int64_t)queues);
+    budget = std::max<int64_t>(0, budget) / 16 * 16;
+    const int64_t want_filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(budget, vis.max_in_filter_bytes);
     const size_t filt = (size_t)((want_filt + 15) / 16 * 16);
-    s.smem = filt + (size_t)warps_per_cta * pt::scan_warp_smem_bytes((int)vis.in_edges.size());
+    s.smem = filt + queues;
     s.filter_smem = filt;
+    // a cluster when some incoming filter may not fit one CTA's budget
+    if (ctx->max_cluster > 1 && filt > 0 && vis.max_single_filter_bytes > (int64_t)filt) s.cluster = ctx->max_cluster;
     int fit = pt::scan_max_ctas_per_sm(ctx->fcfg.block_bits, s.block, s.smem);
     if (fit < 1) fit = 1;
     if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
-    const int64_t max_grid = (int64_t)ctx->num_sms * fit;
-    const int64_t want_warps = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;  // at least a round each
+    int64_t max_grid = (int64_t)ctx->num_sms * fit;
+    max_grid = std::max<int64_t>(s.cluster, max_grid / s.cluster * s.cluster);
+    const int64_t want_warps = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;  // at least a chunk each
     int64_t grid = (want_warps + warps_per_cta - 1) / warps_per_cta;
-    grid = std::max<int64_t>(1, std::min(grid, max_grid));
+    grid = (grid + s.cluster - 1) / s.cluster * s.cluster;
+    grid = std::max<int64_t>(s.cluster, std::min(grid, max_grid));
     s.grid = (int)grid;
     s.total_warps = (int)(grid * warps_per_cta);
     int64_t wpw = (n_words + s.total_warps - 1) / s.total_warps;
@@ -312,6 +327,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     a.words_per_warp = sh.words_per_warp;
     a.total_warps = sh.total_warps;
     a.smem_words = (int32_t)(sh.filter_smem / 4);
+    a.cluster = sh.cluster;
     for (int i = 0; i < a.n_in; ++i) {
         const int e = vis.in_edges[i];
         const pt_edge& ed = ctx->edges[e];
@@ -354,17 +370,11 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
 // attributes are not stream work).
 pt_status prepare_shapes(pt_ctx* ctx) {
     if (ctx->shapes_ready) return PT_OK;
-    size_t max_smem = 0;
-    for (int p = 0; p < 2; ++p)
-        for (Visit& vis : ctx->visits[p]) {
-            const int64_t filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(ctx->smem_budget, vis.max_in_filter_bytes);
-            max_smem = std::max(max_smem, (size_t)((filt + 15) / 16 * 16) + (size_t)(ctx->scan_threads / 32) *
-                                                  pt::scan_warp_smem_bytes((int)vis.in_edges.size()));
-        }
+    // the kernels' shared-memory limit first (occupancy queries depend on it)
     const int bi = ctx->fcfg.block_bits == 512 ? 1 : 0;
-    if ((int)max_smem > ctx->smem_attr_set[bi]) {
-        PT_CUDA(ctx, pt::scan_set_smem_limit(ctx->fcfg.block_bits, max_smem));
-        ctx->smem_attr_set[bi] = (int)max_smem;
+    if ((int)kScanCtaSmem > ctx->smem_attr_set[bi]) {
+        PT_CUDA(ctx, pt::scan_set_smem_limit(ctx->fcfg.block_bits, kScanCtaSmem));
+        ctx->smem_attr_set[bi] = (int)kScanCtaSmem;
     }
     for (int p = 0; p < 2; ++p)
         for (Visit& vis : ctx->visits[p]) vis.shape = scan_shape(ctx, vis);
@@ -592,6 +602,7 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                 if (into == vis.table) {
                     vis.in_edges.push_back(e);
                     vis.max_in_filter_bytes += ctx->filt_max_words[e] * 4;
+                    vis.max_single_filter_bytes = std::max(vis.max_single_filter_bytes, ctx->filt_max_words[e] * 4);
                 }
                 if (from == vis.table) {
                     vis.out_edges.push_back(e);
@@ -853,6 +864,19 @@ pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes,
     ctx->scan_threads = threads;
     ctx->smem_budget = smem_filter_bytes / 16 * 16;
     ctx->ctas_per_sm = ctas_per_sm;
+    ctx->shapes_ready = false;
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return PT_OK;
+}
+
+pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (max_cluster != 1 && max_cluster != 2 && max_cluster != 4)
+        return fail(ctx, PT_ERR_INVALID, "max_cluster %d (1, 2 or 4)", max_cluster);
+    ctx->max_cluster = max_cluster;
     ctx->shapes_ready = false;
     if (ctx->gexec) {
         cudaGraphExecDestroy(ctx->gexec);

@@ -49,7 +49,8 @@ constexpr int kScanWarps = 8;            // batched scan CTA: 256 threads
 constexpr int64_t kTileWords = 4096;     // scan task = 4096 bitmap words = 128k rows
 constexpr int kClearParts = 16;
 constexpr int kInsertParts = 64;
-constexpr int kFilterSmem = 48 * 1024;   // shared-memory filter budget of a batched scan CTA
+constexpr int kFilterSmem = 60 * 1024;   // shared-memory filter budget of a batched scan CTA
+constexpr int kCluster = 4;              // batched scan CTAs per cluster: a filter may spread over 4 CTAs
 constexpr size_t kAl = 256;
 constexpr int kLaunchesPerLevel = 3;     // scan, size/clear, insert
 constexpr int kMetaWordsPerPass = kMaxInst * 3 + kMaxQEdges;  // count, 2 sector counters per instance; nblocks per edge
@@ -265,9 +266,11 @@ pt_status plan_query(pt_server* S, Query* q) {
                 vis.level = std::max(vis.level, lvl[b] + 1);
             }
             lvl[vis.inst] = vis.level;
+            // scan tasks: tiles of kTileWords words, each run by a cluster of kCluster CTAs
             const int64_t words = (n[vis.inst] + 31) / 32;
             vis.grid = std::max<int64_t>(1, (words + kTileWords - 1) / kTileWords);
-            int64_t wpw = (words + vis.grid * kScanWarps - 1) / (vis.grid * kScanWarps);
+            const int64_t ctas = vis.grid * kCluster;
+            int64_t wpw = (words + ctas * kScanWarps - 1) / (ctas * kScanWarps);
             wpw = std::max<int64_t>(32, (wpw + 31) / 32 * 32);
             vis.wpw = (int)wpw;
             q->levels[p] = std::max(q->levels[p], vis.level + 1);
@@ -293,7 +296,7 @@ pt_status plan_query(pt_server* S, Query* q) {
             int64_t g = 1;
             for (const QVisit& vis : q->visits[0])
                 if (vis.inst == v) g = vis.grid;
-            off += al((size_t)g * kScanWarps * 4);
+            off += al((size_t)g * kCluster * kScanWarps * 4);
         }
     }
     for (int e = 0; e < E; ++e) {
@@ -340,8 +343,9 @@ void fill_args(pt_server* S, const Query* q, int p, const QVisit& vis, unsigned 
     a.n_in = (int)vis.in_edges.size();
     a.n_out = (int)vis.out_edges.size();
     a.words_per_warp = vis.wpw;
-    a.total_warps = (int)(vis.grid * kScanWarps);
+    a.total_warps = (int)(vis.grid * kCluster * kScanWarps);
     a.smem_words = kFilterSmem / 4;
+    a.cluster = kCluster;
     for (int i = 0; i < a.n_in; ++i) {
         const int e = vis.in_edges[i];
         const pt_edge& ed = q->edges[e];
@@ -391,8 +395,8 @@ pt_status enqueue_batch_launches(pt_server* S, Slot& sl, int lf, int lb) {
     for (int p = 0; p < 2; ++p) {
         const int L = p == 0 ? lf : lb;
         for (int l = 0; l < L; ++l) {
-            SRV_CUDA(pt::launch_scan_batch(visits, tasks, ranges + 2 * launch_index(p, l, 0), S->fcfg, S->scan_grid,
-                                           kScanWarps * 32, S->scan_smem, sl.stream));
+            SRV_CUDA(pt::launch_scan_batch(visits, tasks, ranges + 2 * launch_index(p, l, 0), S->fcfg, kCluster,
+                                           S->scan_grid, kScanWarps * 32, S->scan_smem, sl.stream));
             SRV_CUDA(pt::launch_size_clear_batch(visits, tasks, ranges + 2 * launch_index(p, l, 1), kClearParts,
                                                  S->fcfg, S->clear_grid, 512, sl.stream));
             SRV_CUDA(pt::launch_insert_batch(visits, tasks, ranges + 2 * launch_index(p, l, 2), kInsertParts, S->fcfg,
@@ -701,7 +705,7 @@ pt_status pt_server_start(pt_server* S) {
     S->scan_smem = (size_t)kFilterSmem + (size_t)kScanWarps * pt::scan_warp_smem_bytes(kMaxInst - 1);
     SRV_CUDA(pt::scan_batch_set_smem_limit(S->fcfg.block_bits, S->scan_smem));
     const int fit = std::max(1, pt::scan_batch_max_ctas_per_sm(S->fcfg.block_bits, kScanWarps * 32, S->scan_smem));
-    S->scan_grid = S->num_sms * fit;
+    S->scan_grid = S->num_sms * fit / kCluster * kCluster;
     S->clear_grid = S->num_sms * 2;
     S->insert_grid = S->num_sms * 2;
     S->started = true;

@@ -88,6 +88,7 @@ _SIGS = {
     "pt_get_visit_stats": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(pt_visit_stats)]),
     "pt_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "pt_set_kernel_timing": (C.c_int, [_P, C.c_int32]),
+    "pt_set_cluster": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "pt_get_launch_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
@@ -234,6 +235,10 @@ def pt_get_visit_stats(ctx: int, pass_: int, table_id: int) -> dict:
 
 def pt_set_launch(ctx: int, threads: int, smem_filter_bytes: int, ctas_per_sm: int = 0) -> None:
     _check(lib.pt_set_launch(ctx, threads, smem_filter_bytes, ctas_per_sm), "pt_set_launch", ctx)
+
+
+def pt_set_cluster(ctx: int, max_cluster: int) -> None:
+    _check(lib.pt_set_cluster(ctx, max_cluster), "pt_set_cluster", ctx)
 
 
 def pt_set_kernel_timing(ctx: int, on: bool) -> None:

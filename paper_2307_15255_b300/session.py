@@ -37,7 +37,8 @@ class TransferSession:
     def __init__(self, tables: Sequence[Tuple[int, Sequence[torch.Tensor], Optional[torch.Tensor]]],
                  edges: Sequence[tuple], bits_per_key: int = 10, k: int = 4, block_bits: int = 256,
                  seed: int = 0, stream: Optional[torch.cuda.Stream] = None,
-                 launch: Optional[Tuple[int, int, int]] = None, graph: bool = False):
+                 launch: Optional[Tuple[int, int, int]] = None, graph: bool = False,
+                 cluster: Optional[int] = None):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.block_bits = block_bits
         self.ctx = _pt.pt_create(bits_per_key, k, block_bits, seed, self.stream.cuda_stream)
@@ -59,6 +60,8 @@ class TransferSession:
             _pt.pt_set_join_graph(self.ctx, self.edges)
             if launch is not None:
                 _pt.pt_set_launch(self.ctx, *launch)
+            if cluster is not None:
+                _pt.pt_set_cluster(self.ctx, cluster)
             self.order, self.mem_bytes = _pt.pt_plan(self.ctx, len(self.n_rows))
             if graph:
                 _pt.pt_set_graph_mode(self.ctx, True)

@@ -25,9 +25,9 @@ def edges_of(w):
     return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1)) for e in w.edges]
 
 
-def session_for(w, launch=None, graph=False, host=False, pin=False):
+def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None):
     return TransferSession(device_tables(w, host, pin), edges_of(w), w.bits_per_key, w.k, w.block_bits,
-                           w.seed, launch=launch, graph=graph)
+                           w.seed, launch=launch, graph=graph, cluster=cluster)
 
 
 def collect(s, w):

@@ -57,6 +57,14 @@ def test_launch_shapes_give_identical_results(oracle_lib, launch):
     _check(W.snowflake(scale=0.03, bits_per_key=16), oracle_lib, launch=launch)
 
 
+@pytest.mark.parametrize("cluster,smem", [(1, 8 * 1024), (2, 8 * 1024), (4, 8 * 1024), (4, 2 * 1024),
+                                          (4, 96 * 1024)])
+def test_cluster_spread_filters(oracle_lib, cluster, smem):
+    # small shared-memory budgets push the filters into the cluster-spread (or global) path
+    _check(W.snowflake(scale=0.03, int64=True, composite=True, bits_per_key=16), oracle_lib,
+           launch=(256, smem, 0), cluster=cluster)
+
+
 def test_random_tiny_graphs(oracle_lib):
     for s in range(60):
         w = W.random_tiny(7000 + s, 2 + s % 5, max_rows=200, domain=40, acyclic=(s % 3 != 0),
