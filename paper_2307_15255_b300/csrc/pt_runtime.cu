@@ -91,7 +91,7 @@ struct pt_ctx {
 
     int scan_threads = 256;
     int smem_budget = 96 * 1024;
-    int max_cluster = 4;  // 1: no clusters
+    int max_cluster = 1;  // 1: no clusters (remote probes measured slower than L2 ones)
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
     bool shapes_ready = false;

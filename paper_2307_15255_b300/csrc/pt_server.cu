@@ -50,7 +50,7 @@ constexpr int64_t kTileWords = 4096;     // scan task = 4096 bitmap words = 128k
 constexpr int kClearParts = 16;
 constexpr int kInsertParts = 64;
 constexpr int kFilterSmem = 60 * 1024;   // shared-memory filter budget of a batched scan CTA
-constexpr int kCluster = 4;              // batched scan CTAs per cluster: a filter may spread over 4 CTAs
+constexpr int kCluster = 1;              // batched scan CTAs per cluster (1: no cluster-spread filters)
 constexpr size_t kAl = 256;
 constexpr int kLaunchesPerLevel = 3;     // scan, size/clear, insert
 constexpr int kMetaWordsPerPass = kMaxInst * 3 + kMaxQEdges;  // count, 2 sector counters per instance; nblocks per edge
