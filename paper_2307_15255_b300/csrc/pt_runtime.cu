@@ -90,7 +90,7 @@ struct pt_ctx {
     int64_t seg_cap = 0;
 
     int scan_threads = 256;
-    int smem_budget = 96 * 1024;
+    int smem_budget = 40 * 1024;  // more shared memory means less L1 for the filters probed through it
     int max_cluster = 1;  // 1: no clusters (remote probes measured slower than L2 ones)
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
