@@ -398,6 +398,14 @@ def ours(args) -> None:
         s.close()
         return
 
+    # launch shape from the autotuner (outside the timed region)
+    tuned = None
+    if not args.no_autotune and launch is None:
+        from paper_2307_15255_b300 import autotune
+        tuned = autotune.tune(s, use_cache=False)
+        tuned = {"launch": list(tuned["launch"]), "ms": tuned["ms"],
+                 "trials": [[list(l), m] for l, m in tuned["trials"]]}
+
     # accounting of one run (identical every step: same inputs)
     s.run()
     torch.cuda.synchronize()
@@ -539,6 +547,7 @@ def ours(args) -> None:
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": launches,
+        "autotune": tuned,
         "scale_mode": "replicas" if world > 1 else "single",
         "serving": serving,
     }
@@ -562,6 +571,7 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-scale", type=float, default=1.0, help="star size (1 = fact 100M rows)")
     ap.add_argument("--serving-queries", type=int, default=2000)
     ap.add_argument("--serving-single", type=int, default=200, help="queries timed one at a time")

@@ -41,6 +41,9 @@ class TransferSession:
                  cluster: Optional[int] = None):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.block_bits = block_bits
+        self.bits_per_key = bits_per_key
+        self.k = k
+        self.col_dtypes = []
         self.ctx = _pt.pt_create(bits_per_key, k, block_bits, seed, self.stream.cuda_stream)
         self._keep: List[torch.Tensor] = []
         self.n_rows = []
@@ -56,6 +59,7 @@ class TransferSession:
                     sp, sm = sel.data_ptr(), _mem(sel)
                 _pt.pt_register_table(self.ctx, int(n), spec, sp, sm)
                 self.n_rows.append(int(n))
+                self.col_dtypes.append([str(c.dtype) for c in cols])
             self.edges = [tuple(e) for e in edges]
             _pt.pt_set_join_graph(self.ctx, self.edges)
             if launch is not None:

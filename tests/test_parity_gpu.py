@@ -198,3 +198,20 @@ def test_kernel_timing_direct_and_graph():
         assert P.pt_get_launch_count(s.ctx) - n0 == 3 * (P.pt_get_launch_count(s.ctx) - n0) // 3 > 0
     finally:
         s.close()
+
+
+def test_autotuner_keeps_results_exact(oracle_lib, tmp_path):
+    from _gpu import assert_same, collect, session_for
+    from paper_2307_15255_b300 import autotune
+    w = W.snowflake(scale=0.02, bits_per_key=16)
+    s = session_for(w)
+    try:
+        cache = str(tmp_path / "tune.json")
+        r = autotune.tune(s, candidates=[(256, 40 * 1024, 0), (128, 0, 0)], runs=2, cache_path=cache)
+        assert not r["cached"] and len(r["trials"]) == 2
+        r2 = autotune.tune(s, cache_path=cache)
+        assert r2["cached"] and tuple(r2["launch"]) == tuple(r["launch"])
+        s.run()
+        assert_same(collect(s, w), oracle_lib.transfer(w), w)
+    finally:
+        s.close()
