@@ -358,6 +358,22 @@ def committed_traffic(workload: str, bpk: int):
     return None if ent is None else ent.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's step time (every rank runs its own replica)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(rows_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank's rows over the slowest rank's time."""
+    return rows_per_rank * world / (ms * 1e-3)
+
+
 def ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -455,12 +471,8 @@ def ours(args) -> None:
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
     launches = P.pt_get_launch_count(s.ctx) - launches0
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
 
     # per-kernel times: the same graph recaptured with CUDA events around every
     # scan launch (event-record nodes on the launching stream), replayed the
@@ -526,7 +538,7 @@ def ours(args) -> None:
         cpu = oracle_timing(w, args.cpu_seconds)
     line = {
         "metric": "transfer rows/s",
-        "value": rows * world / (ms * 1e-3),
+        "value": job_rows_per_s(rows, world, ms),
         "unit": "rows/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms,

@@ -149,7 +149,9 @@ pt_status pt_set_join_graph(pt_ctx* ctx, int32_t n_edges, const pt_edge* edges);
  * forward pass and in the reverse order in the backward pass.  Allocates
  * all device memory a run needs.  order_out (nullable, n_tables entries)
  * receives the forward visiting order; mem_bytes_out (nullable) the bytes
- * of device memory allocated.  Errors: PT_ERR_OOM, PT_ERR_INVALID. */
+ * of device memory allocated.  Errors: PT_ERR_OOM (also forced, without any
+ * device allocation, when the environment variable PT_INJECT_OOM is "1"),
+ * PT_ERR_INVALID. */
 pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out);
 
 /* Forward pass: visit every table in topological order of the transfer

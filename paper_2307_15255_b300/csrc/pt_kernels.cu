@@ -485,8 +485,10 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                             load8(sub_row0 + 32u * (g + 8), kn);
                         else if (next_dense)
                             load8(sub_row0 + 1024u, kn);
+                        if (d_col.dtype != kHashed) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) h[i] = d_col.dtype == kHashed ? h[i] : hash_key(h[i], seed);
+                            for (int i = 0; i < 8; ++i) h[i] = hash_key(h[i], seed);
+                        }
                         bool pass[8];
                         if (off >= 0 && !s_split[0]) {
 #pragma unroll

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -676,7 +677,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         off += ctx->meta_bytes;
     }
     void* arena = nullptr;
-    if (cudaMalloc(&arena, off) != cudaSuccess) {
+    // PT_INJECT_OOM=1 makes this allocation fail on the host (tests of the error path)
+    const char* inject = getenv("PT_INJECT_OOM");
+    if ((inject && inject[0] == '1') || cudaMalloc(&arena, off) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PT_ERR_OOM, "device arena of %zu bytes", off);
     }

@@ -215,3 +215,30 @@ def test_autotuner_keeps_results_exact(oracle_lib, tmp_path):
         assert_same(collect(s, w), oracle_lib.transfer(w), w)
     finally:
         s.close()
+
+
+def test_injected_allocation_failure_reports_oom(monkeypatch):
+    import paper_2307_15255_b300.pt as P
+    ctx = P.pt_create()
+    try:
+        x = torch.arange(64, dtype=torch.int32, device="cuda")
+        P.pt_register_table(ctx, 64, [(x.data_ptr(), P.PT_I32, P.PT_MEM_DEVICE)])
+        P.pt_register_table(ctx, 64, [(x.data_ptr(), P.PT_I32, P.PT_MEM_DEVICE)])
+        P.pt_set_join_graph(ctx, [(0, (0,), 1, (0,))])
+        monkeypatch.setenv("PT_INJECT_OOM", "1")
+        with pytest.raises(P.PtError) as ei:
+            P.pt_plan(ctx, 2)
+        assert ei.value.status == P.PT_ERR_OOM
+        monkeypatch.delenv("PT_INJECT_OOM")
+        P.pt_plan(ctx, 2)  # the context is still usable
+        P.pt_run_transfer(ctx)
+        assert P.pt_get_survivors(ctx, 1, None) == 64
+    finally:
+        P.pt_destroy(ctx)
+
+
+def test_server_arena_too_large_reports_oom():
+    import paper_2307_15255_b300.pt as P
+    with pytest.raises(P.PtError) as ei:
+        P.pt_server_create(arena_bytes=1 << 52)
+    assert ei.value.status == P.PT_ERR_OOM
