@@ -107,3 +107,18 @@ def test_server_rejects_bad_queries(star):
             P.pt_server_poll(srv, t)
     finally:
         P.pt_server_destroy(srv)
+
+
+@pytest.mark.slow
+def test_served_full_size_star_samples(oracle_lib):
+    """The serving workload at full size (fact 100M rows): a few queries of a
+    batch, checked against the oracle bit for bit."""
+    w = W.star(scale=1.0, bits_per_key=16)
+    pool = W.selection_pool(w, size=8)
+    qs = W.serving_queries(w, 6, rate_qps=0, pool=pool)
+    got = run_server(w, qs, 8, 2, 48 << 30, device_sel=True)
+    for q, res in list(zip(qs, got))[:3]:
+        want = oracle_lib.transfer(query_workload(w, q))
+        for j, (bm, c) in enumerate(res):
+            assert np.array_equal(bm, want["surv"][1][j]), (q.inst_table, j)
+            assert c == want["count"][1][j]
