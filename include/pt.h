@@ -106,7 +106,9 @@ typedef struct {
     int32_t n_in;          /* incoming edges in this pass */
     int32_t n_out;         /* outgoing edges in this pass */
     int32_t has_input_bitmap;
-    int32_t reserved;
+    int32_t first_probe;   /* 1: the visit's first probe ran as its own pass
+                              (pt_set_first_probe) */
+    int64_t first_probe_sectors; /* the part of probe_sectors that pass read */
 } pt_visit_stats;
 
 /* Version of this ABI: (major << 16) | minor. */
@@ -204,17 +206,39 @@ pt_status pt_set_launch(pt_ctx* ctx, int32_t threads, int32_t smem_filter_bytes,
  * slower than probes through L1/L2), 2 or 4.  Takes effect at the next run. */
 pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
 
+/* First-probe passes (on by default).  A forward-pass visit of a table
+ * without a selection bitmap, with incoming edges and at least 2^20 rows,
+ * starts with every row alive; its first probe in probe order is then a
+ * plain stream over that edge's key column(s), run as a separate kernel
+ * with twice the resident warps of the scan kernel.  It writes the rows
+ * that pass as a bitmap, and the scan kernel runs the visit's other probes
+ * on it.  Results and sector accounting are the same either way; enable = 0
+ * keeps every probe in the scan kernel.  Takes effect at the next run. */
+pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable);
+
 /* Kernel timing.  pt_set_kernel_timing(ctx, 1) records CUDA events around
- * every scan (probe + compact) launch and around every visit's size/clear +
- * insert pair, on the stream each runs on.  Direct launches accumulate
- * from the moment timing is switched on.  In graph mode the events are
- * part of the captured graph (external event-record nodes; switching timing
- * recaptures), so their values are those of the most recent replay.
- * pt_get_kernel_time returns the summed milliseconds and counts of both.
- * Synchronizes the context's stream. */
+ * every first-probe launch, every scan (probe + compact) launch and every
+ * visit's size/clear + insert pair, on the stream each runs on.  Direct
+ * launches accumulate from the moment timing is switched on.  In graph mode
+ * the events are part of the captured graph (external event-record nodes;
+ * switching timing recaptures), so their values are those of the most
+ * recent replay.  pt_get_kernel_time returns the summed milliseconds and
+ * counts of the probe phase (first-probe and scan launches) and of the
+ * build phase (size/clear + insert pairs); pt_get_kernel_times returns the
+ * three kinds apart.  Both synchronize the context's stream. */
+typedef struct {
+    double first_ms;        /* first-probe launches */
+    double scan_ms;         /* scan launches */
+    double build_ms;        /* size/clear + insert pairs */
+    int32_t first_launches;
+    int32_t scan_launches;
+    int32_t build_pairs;
+    int32_t reserved;
+} pt_kernel_times;
 pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on);
 pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
                              int32_t* other_launches);
+pt_status pt_get_kernel_times(pt_ctx* ctx, pt_kernel_times* out);
 
 /* Number of kernels the library launched since the context was created
  * (a graph replay counts each of its kernel nodes). */

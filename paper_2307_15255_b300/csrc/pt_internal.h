@@ -13,20 +13,24 @@ constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
 constexpr int kRoundWords = 128;  // bitmap words (32 rows each) a scan warp takes per round
 constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words
 constexpr int kDrain = 64;        // a probe stage runs once its queue holds this many rows
-constexpr int kQueueCap = 128;    // row-id queue in front of a probe stage (per warp) ...
-constexpr int kQueueCapBig = 320; // ... except stage 1's, which takes 8 dense words (256 rows) at once
+constexpr int kQueueCap = kDrain + 256;  // row-id queue in front of a probe stage (per warp): room for
+                                         // a drain's worth plus 8 dense words (256 rows) or a sparse sub-round
 constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
 constexpr int kScanMinBlocks = 2;     // scan CTAs per SM the register budget allows
+constexpr int kFirstThreads = 256;    // first-probe CTA size (launch bounds)
+constexpr int kFirstMinBlocks = 3;    // first-probe CTAs per SM the register budget allows
+constexpr int kFirstTileRows = 256;   // rows a first-probe warp takes at a time (8 bitmap words)
+constexpr int64_t kFirstMinRows = 1 << 20;  // smaller visits keep their first probe in the scan kernel
 
 // Word offset of stage s's queue inside a warp's queue area, and the area's size.
-__host__ __device__ inline int qoff(int s) { return s * kQueueCap + (s >= 2 ? kQueueCapBig - kQueueCap : 0); }
-__host__ __device__ inline int scan_queue_words(int n_in) { return n_in == 0 ? 0 : qoff(n_in - 1) + (n_in == 2 ? kQueueCapBig : kQueueCap); }
+__host__ __device__ inline int qoff(int s) { return s * kQueueCap; }
+__host__ __device__ inline int scan_queue_words(int n_in) { return n_in * kQueueCap; }
 
 // Shared memory a scan CTA needs besides its filter budget: per warp, one
-// queue and one round of "alive before this probe" words per incoming edge,
-// plus the round's survivor words.
+// queue per incoming edge, the round's survivor words and the last row
+// that entered each stage.
 __host__ __device__ inline size_t scan_warp_smem_bytes(int n_in) {
-    return (size_t)(scan_queue_words(n_in) + n_in * kRoundWords + kRoundWords) * 4;
+    return (size_t)(scan_queue_words(n_in) + kRoundWords + kMaxIn) * 4;
 }
 
 constexpr int32_t kHashed = 2;  // column dtype: uint64 values that already are H(key)
@@ -80,7 +84,8 @@ struct VisitArgs {
     uint32_t* ids;                   // compacted survivor row ids (nullptr: visit builds nothing)
     uint32_t* seg_count;             // survivors per scan warp (segment), nullptr if ids is
     unsigned long long* count;       // total survivors (zeroed before the pass)
-    unsigned long long* stats;       // [0] probe sectors, [1] build sectors (zeroed before the pass)
+    unsigned long long* stats;       // [0] probe sectors, [1] build sectors (zeroed before the pass);
+                                     // [2] the part of [0] a first-probe pass read (only with one)
     int32_t n_in;
     int32_t n_out;
     int32_t n_bcols;
@@ -89,6 +94,8 @@ struct VisitArgs {
     int32_t total_warps;             // scan warps launched (= segments)
     int32_t cluster;                 // CTAs per thread-block cluster of the scan (1, 2 or 4)
     int32_t pad_;
+    const int32_t* first_in;         // in[] index of the edge a first-probe pass already tested
+                                     // (in_bits then holds its survivors), or nullptr
     ProbeEdge in[kMaxIn];
     BuildEdge out[kMaxOut];
     ColRef bcol[kMaxBuildCols];
@@ -103,6 +110,16 @@ struct BatchTask {
 };
 
 // Launchers (return the launch error, if any).
+//
+// launch_probe_first: the first probe (in probe order) of a visit whose rows
+// are all alive (a.in_bits is ignored).  Records the in[] index of that edge
+// at *first, writes the rows that pass it to `mid` (ceil(n/32) words) and adds
+// its key sectors to a.stats[2] and a.stats[0].  The filter is copied into
+// shared memory when it fits smem_words; smem is the dynamic shared memory
+// of the launch (>= smem_words * 4).
+cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t* mid, int32_t* first,
+                               int32_t smem_words, int grid, int block, size_t smem, cudaStream_t s);
+int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem);
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);

@@ -155,6 +155,49 @@ __device__ __forceinline__ bool probe_global(const uint32_t* __restrict__ f, uin
     return ok & 1u;
 }
 
+// Probes of R keys at once.  In shared memory, every key tests its k bits
+// (measured faster than skipping loads, which costs branches on an
+// ALU-bound stream).  Through L1/L2, in two steps: step 1 tests bit 0 of
+// every key -- a key that is not in the filter fails it with probability
+// 1 - (fill of its block), about 78% at 16 bits per key -- and step 2 tests
+// bits 1..k-1 only for the keys that passed, so lanes whose key failed
+// issue no load and take no L1 tag lookup.  The verdicts equal the
+// one-key probes above: all k bits set.
+template <int B, int KT, int R>
+__device__ __forceinline__ void probe_shared_n(uint32_t sbase, uint32_t nb, const uint64_t* h, int k, bool* pass) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) pass[i] = probe_shared<B, KT>(sbase, nb, h[i], k);
+}
+
+template <int B, int KT, int R>
+__device__ __forceinline__ void probe_global_n(const uint32_t* __restrict__ f, uint32_t nb, const uint64_t* h, int k,
+                                               bool* pass) {
+    using BB = BlockBits<B>;
+    uint32_t lo[R], bi[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        lo[i] = (uint32_t)h[i];
+        bi[i] = mul_hi((uint32_t)(h[i] >> 32), nb);
+        const uint32_t w0 = mul_hi(mad_lo(lo[i], BB::SCALE, 0u), BB::WPB);
+        pass[i] = rot_r(__ldg(f + (size_t)bi[i] * BB::WPB + w0), lo[i]) & 1u;
+    }
+    const int kk = KT > 0 ? KT : k;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if (pass[i]) {
+            const uint32_t* blk = f + (size_t)bi[i] * BB::WPB;
+            const uint32_t h2 = (lo[i] >> 16) | 1u;
+            uint32_t ok = 0xFFFFFFFFu;
+#pragma unroll 4
+            for (int t = 1; t < kk; ++t) {
+                const uint32_t at = mad_lo((uint32_t)t, h2, lo[i]);
+                ok &= rot_r(__ldg(blk + mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB)), at);
+            }
+            pass[i] = ok & 1u;
+        }
+    }
+}
+
 // Probe a filter spread over the CTAs of a cluster of 2^lc CTAs: block j is
 // block j >> lc of the part held by CTA j & (2^lc - 1), at byte address
 // sbase in every CTA's shared window.
@@ -180,16 +223,24 @@ __device__ __forceinline__ bool probe_cluster(uint32_t sbase, uint32_t lc, uint3
 // 1. scan: probe every incoming filter, write the survivor bitmap, compact
 //
 // Each warp owns a contiguous chunk of bitmap words and walks it in rounds
-// of 32 words (1024 rows): one coalesced load brings the round's input
-// words, one per lane.  Rows still alive wait in a per-warp queue in front
-// of each probe stage (incoming edges in probe order); a stage runs once
-// its queue holds 128 rows, four rows per lane, so every probe works on
-// densely packed live rows and each lane has four independent key loads in
-// flight.  Survivors of a stage are appended, in row order, to the next
-// stage's queue; survivors of the last stage set their bit in the round's
-// output words.  At the end of a round the queues are flushed, the 32
-// survivor words are stored, and their row ids are compacted into the
-// warp's segment of the id array with ballot/popc ranks.
+// of 128 words (4096 rows): one coalesced load brings four input words per
+// lane.  Rows still alive wait in a per-warp queue in front of each probe
+// stage (incoming edges in probe order); a stage runs once its queue holds
+// kDrain rows, kDrain/32 rows per lane, so every probe works on densely
+// packed live rows and each lane has independent key loads in flight.
+// Survivors of a stage are appended, in row order, to the next stage's
+// queue; survivors of the last stage set their bit in the round's output
+// words in shared memory, which are stored at the end of the round.  The
+// queues are not emptied at round ends: on a sparse input they fill over
+// several rounds, so the stages keep running full batches, and rows queued
+// in an earlier round set their output bit directly in the bitmap.  After
+// the chunk's last round the queues are flushed, and the survivors' row
+// ids are compacted into the warp's segment of the id array from its
+// finished output words.
+//
+// Sector accounting: rows enter every stage in ascending row order, so the
+// key sectors a stage reads are the rows whose sector differs from that of
+// the row that entered the same stage before them.
 // ---------------------------------------------------------------------------
 // Shared state of one scan CTA besides the dynamic filter/queue area.
 struct ScanShared {
@@ -197,7 +248,38 @@ struct ScanShared {
     int32_t off[kMaxIn];   // word offset of the filter in smem, or -1: probe from global
     uint32_t nb[kMaxIn];
     uint32_t split[kMaxIn];  // 1: the filter is spread over the cluster (this CTA holds its part)
+    int32_t n_in;            // edges this kernel probes (a first-probe pass may have taken one)
 };
+
+// Probe order (LIP-style): incoming edges by ascending survivors/rows of the
+// building visit, ties by edge id, with in[skip] left out (skip < 0: none).
+// Writes the in[] indexes to ord and returns their number.  One thread.
+__device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord) {
+    unsigned long long c[kMaxIn];
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i) {
+        c[i] = i < a.n_in ? *a.in[i].build_count : 0ull;
+        if (i < a.n_in && i != skip) ord[m++] = i;
+    }
+    for (int i = 1; i < m; ++i) {
+        const int x = ord[i];
+        int j = i - 1;
+        while (j >= 0) {
+            const int y = ord[j];
+            const unsigned long long lhs = c[x] * (unsigned long long)a.in[y].build_rows;
+            const unsigned long long rhs = c[y] * (unsigned long long)a.in[x].build_rows;
+            if (lhs < rhs || (lhs == rhs && a.in[x].edge_id < a.in[y].edge_id)) {
+                ord[j + 1] = ord[j];
+                --j;
+            } else {
+                break;
+            }
+        }
+        ord[j + 1] = x;
+    }
+    return m;
+}
 
 // One CTA of a visit's scan: `cta` is its index in the visit's grid of
 // total_warps / (blockDim.x / 32) CTAs.  Every thread of the block calls it.
@@ -215,36 +297,15 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);  // shared-window address of the filters
 
     if (threadIdx.x == 0) {
-        // LIP-style order: ascending survivors/rows of the building visit, ties by edge id.
         int ord[kMaxIn];
-        unsigned long long c[kMaxIn];
-#pragma unroll
-        for (int i = 0; i < kMaxIn; ++i) {
-            ord[i] = i;
-            c[i] = i < a.n_in ? *a.in[i].build_count : 0ull;
-        }
-        for (int i = 1; i < a.n_in; ++i) {
-            const int x = ord[i];
-            int j = i - 1;
-            while (j >= 0) {
-                const int y = ord[j];
-                const unsigned long long lhs = c[x] * (unsigned long long)a.in[y].build_rows;
-                const unsigned long long rhs = c[y] * (unsigned long long)a.in[x].build_rows;
-                if (lhs < rhs || (lhs == rhs && a.in[x].edge_id < a.in[y].edge_id)) {
-                    ord[j + 1] = ord[j];
-                    --j;
-                } else {
-                    break;
-                }
-            }
-            ord[j + 1] = x;
-        }
+        const int m = lip_order(a, a.first_in ? *a.first_in : -1, ord);
+        sh.n_in = m;
         // Shared-memory placement, greedily in probe order: a whole copy in
         // every CTA when it fits, else (in a cluster) 1/C of it in each CTA of
         // the cluster, else probed from global memory.  Every CTA of a cluster
         // computes the same placement from the same counts.
         int32_t used = 0;
-        for (int i = 0; i < a.n_in; ++i) {
+        for (int i = 0; i < m; ++i) {
             const ProbeEdge& pe = a.in[ord[i]];
             s_pe[i] = pe;
             const uint32_t nb = (uint32_t)*pe.nblocks;
@@ -265,7 +326,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         }
     }
     __syncthreads();
-    const int n_in = a.n_in;
+    const int n_in = sh.n_in;
     for (int i = 0; i < n_in; ++i) {
         if (s_off[i] < 0) continue;
         const uint4* src = reinterpret_cast<const uint4*>(s_pe[i].filter);
@@ -289,9 +350,9 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t* wsm = smem + a.smem_words + warp * (uint32_t)(scan_warp_smem_bytes(n_in) / 4);
-    uint32_t* queue = wsm;                                  // row-id queues, stage s at qoff(s)
-    uint32_t* abm = wsm + scan_queue_words(n_in);          // [n_in][kRoundWords] rows entering each stage
-    uint32_t* obm = abm + n_in * kRoundWords;               // [kRoundWords] survivors of the round
+    uint32_t* queue = wsm;                             // row-id queues, stage s at qoff(s)
+    uint32_t* obm = wsm + scan_queue_words(n_in);      // [kRoundWords] survivors of the round
+    uint32_t* last_in = obm + kRoundWords;             // [kMaxIn] last row that entered stage s
 
     const int64_t gw = cta * (blockDim.x >> 5) + warp;
     const int64_t n_words = (a.n + 31) >> 5;
@@ -300,37 +361,58 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     const uint32_t tail_bits = (uint32_t)(a.n & 31);
     const int k = f.k;
     const uint64_t seed = f.seed;
+    constexpr uint32_t kNoRow = 0xFFFFFFFFu;  // rows are below 2^31
 
-    uint32_t local = 0;                     // survivors of this warp (= its segment length)
-    unsigned long long psec = 0, bsec = 0;  // per lane; reduced at the end
-    // queue lengths, 8 bits per stage in one register (warp-uniform; a queue
-    // never holds more than 255 rows: it is drained below kDrain before each append)
-    uint64_t qpack = 0;
-    auto qget = [&](int s) -> uint32_t { return (uint32_t)(qpack >> (8 * s)) & 0xFFu; };
-    auto qset = [&](int s, uint32_t v) {
-        qpack = (qpack & ~(0xFFull << (8 * s))) | ((uint64_t)v << (8 * s));
+    if (lane < (uint32_t)kMaxIn) last_in[lane] = kNoRow;
+    unsigned long long psec = 0;  // per lane; reduced at the end
+    // queue lengths (warp-uniform), 16 bits per stage: stages 0-3 in qlo, 4-7 in qhi
+    uint64_t qlo = 0, qhi = 0;
+    auto qget = [&](int s) -> uint32_t {
+        return (uint32_t)((s < 4 ? qlo : qhi) >> (16 * (s & 3))) & 0xFFFFu;
     };
+    auto qset = [&](int s, uint32_t v) {
+        const uint64_t clear = ~(0xFFFFull << (16 * (s & 3))), put = (uint64_t)v << (16 * (s & 3));
+        if (s < 4)
+            qlo = (qlo & clear) | put;
+        else
+            qhi = (qhi & clear) | put;
+    };
+    __syncwarp();
 
-    // Run stage s on the first cnt (<= kDrain) rows of its queue.
+    // Run stage s on the first cnt (<= kDrain) rows of its queue.  Survivors
+    // of the last stage set their bit in obm when they belong to the round
+    // starting at row round_row0, else (rows queued in an earlier round)
+    // directly in the output bitmap.
     auto run_stage = [&](int s, uint32_t cnt, uint32_t round_row0) {
         uint32_t* q = queue + qoff(s);
         const ColRef c0 = s_pe[s].col[0];
         const ColRef c1 = s_pe[s].col[1];
         const int ncols = s_pe[s].ncols;
+        const uint32_t sh0 = c0.dtype == 0 ? 3u : 2u, sh1 = c1.dtype == 0 ? 3u : 2u;  // log2 rows per sector
         const int32_t off = s_off[s];
         const uint32_t nb = s_nb[s];
         const uint32_t split = s_split[s];
         const uint32_t* fg = s_pe[s].filter;
         const bool last = s == n_in - 1;
         uint32_t* nq = queue + qoff(s + 1);
-        uint32_t* nbm = last ? obm : abm + (s + 1) * kRoundWords;
         uint32_t nn = last ? 0u : qget(s + 1);
-        // survivors move on in row order
+        const uint32_t prev0 = last_in[s];
+        // key sectors: a row whose sector differs from the previous row's entering
+        // this stage (stage 0's are counted from the input words instead)
+        auto count_sectors = [&](uint32_t r, uint32_t prev) {
+            if (s == 0) return;
+            psec += (r >> sh0) != (prev >> sh0);
+            if (ncols == 2) psec += (r >> sh1) != (prev >> sh1);
+        };
         auto emit = [&](bool pass, uint32_t r) {
             const uint32_t m = __ballot_sync(FULL, pass);
             if (pass) {
-                atomicOr(nbm + ((r - round_row0) >> 5), 1u << (r & 31));
-                if (!last) nq[nn + __popc(m & lt_mask)] = r;
+                if (!last)
+                    nq[nn + __popc(m & lt_mask)] = r;
+                else if (r >= round_row0)
+                    atomicOr(obm + ((r - round_row0) >> 5), 1u << (r & 31));
+                else
+                    atomicOr(a.out_bits + (r >> 5), 1u << (r & 31));
             }
             nn += __popc(m);
         };
@@ -340,23 +422,26 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
             uint32_t r[R];
             uint64_t h[R];
 #pragma unroll
-            for (int i = 0; i < R; ++i) r[i] = q[lane + 32u * i];
+            for (int i = 0; i < R; ++i) {
+                const uint32_t idx = lane + 32u * i;
+                r[i] = q[idx];
+                count_sectors(r[i], idx == 0 ? prev0 : q[idx - 1]);
+            }
 #pragma unroll
             for (int i = 0; i < R; ++i) h[i] = edge_hash(c0, c1, ncols, r[i], seed);
             bool pass[R];
             if (off >= 0 && !split) {
-#pragma unroll
-                for (int i = 0; i < R; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+                probe_shared_n<B, KT, R>(sfilt + 4u * (uint32_t)off, nb, h, k, pass);
             } else if (off >= 0) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) pass[i] = probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h[i], k);
             } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                probe_global_n<B, KT, R>(fg, nb, h, k, pass);
             }
-            // keep the unprocessed tail of the queue (fewer than kQueueCapBig - kDrain rows) at its front
+            const uint32_t last_row = q[cnt - 1];
+            // keep the unprocessed tail of the queue (fewer than kQueueCap - kDrain rows) at its front
             const uint32_t rest = qget(s) - cnt;
-            constexpr int RT = (kQueueCapBig - kDrain) / 32;
+            constexpr int RT = (kQueueCap - kDrain) / 32;
             uint32_t keep[RT];
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
@@ -369,17 +454,19 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                 const uint32_t idx = lane + 32u * i;
                 if (idx < rest) q[idx] = keep[i];
             }
+            if (lane == 0) last_in[s] = last_row;
             qset(s, rest);
 #pragma unroll
             for (int i = 0; i < R; ++i) emit(pass[i], r[i]);
         } else {
-            // the rest of a round (cnt < kDrain is the whole queue): 32 rows at a time
+            // the rest of the queue (cnt < kDrain is the whole queue): 32 rows at a time
             for (uint32_t b = 0; b < cnt; b += 32) {
                 const uint32_t idx = b + lane;
                 const bool live = idx < cnt;
                 const uint32_t r = live ? q[idx] : 0u;
                 bool pass = false;
                 if (live) {
+                    count_sectors(r, idx == 0 ? prev0 : q[idx - 1]);
                     const uint64_t h = edge_hash(c0, c1, ncols, r, seed);
                     pass = off < 0   ? probe_global<B, KT>(fg, nb, h, k)
                            : split ? probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h, k)
@@ -387,6 +474,9 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                 }
                 emit(pass, r);
             }
+            const uint32_t last_row = q[cnt - 1];
+            __syncwarp();
+            if (lane == 0) last_in[s] = last_row;
             qset(s, 0u);
         }
         if (!last) qset(s + 1, nn);
@@ -432,8 +522,9 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     uint64_t kn[8];  // prefetched keys (valid when have_pref)
     bool have_pref = false;
     constexpr int NS = kRoundWords / 32;  // sub-rounds of 32 words per round
+    const int32_t d00 = n_in > 0 ? s_pe[0].col[0].dtype : 0, d01 = n_in > 0 ? s_pe[0].col[1].dtype : 0;
+    const bool two0 = n_in > 0 && s_pe[0].ncols == 2;
 
-    int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
     uint32_t win[NS], win_next[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) win[q] = load_word(w_begin + 32 * q + lane);
@@ -442,15 +533,18 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         const int64_t rb_next = rb + kRoundWords;
 #pragma unroll
         for (int q = 0; q < NS; ++q) win_next[q] = load_word(rb_next + 32 * q + lane);
-        uint32_t ow[NS];
         if (n_in == 0) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) ow[q] = win[q];
+            for (int q = 0; q < NS; ++q) {
+                const int64_t wl = rb + 32 * q + lane;
+                if (wl < w_end) a.out_bits[wl] = win[q];
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 obm[32 * q + lane] = 0u;
-                for (int s = 0; s < n_in; ++s) abm[s * kRoundWords + 32 * q + lane] = s == 0 ? win[q] : 0u;
+                psec += sectors_of(win[q], d00);  // every input row enters stage 0
+                if (two0) psec += sectors_of(win[q], d01);
             }
             __syncwarp();
 #pragma unroll 1
@@ -469,11 +563,17 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                 const uint32_t sub_row0 = round_row0 + 1024u * q;
                 const bool dense = dense_ok && nw == 32 && __all_sync(FULL, wq == FULL);
                 if (dense) {
+                    // rows still waiting for stage 0 move on first, so that every
+                    // stage keeps receiving its rows in ascending order
+                    if (qget(0) > 0) {
+                        run_stage(0, qget(0), round_row0);
+                        cascade(0, round_row0);
+                    }
                     const int32_t off = s_off[0];
                     const uint32_t nb = s_nb[0];
                     const uint32_t* fg = s_pe[0].filter;
                     const bool last = n_in == 1;
-                    uint32_t* nbm = (last ? obm : abm + kRoundWords) + 32 * q;
+                    uint32_t* nbm = obm + 32 * q;
                     if (!have_pref) load8(sub_row0, kn);
                     const bool next_dense = sb + 64 <= w_end && __all_sync(FULL, wn == FULL);
 #pragma unroll 1
@@ -491,20 +591,18 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                         }
                         bool pass[8];
                         if (off >= 0 && !s_split[0]) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) pass[i] = probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h[i], k);
+                            probe_shared_n<B, KT, 8>(sfilt + 4u * (uint32_t)off, nb, h, k, pass);
                         } else if (off >= 0) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) pass[i] = probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h[i], k);
                         } else {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) pass[i] = probe_global<B, KT>(fg, nb, h[i], k);
+                            probe_global_n<B, KT, 8>(fg, nb, h, k, pass);
                         }
                         uint32_t mk[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             mk[i] = __ballot_sync(FULL, pass[i]);
-                            if (lane == 0) nbm[g + i] = mk[i];
+                            if (last && lane == 0) nbm[g + i] = mk[i];
                         }
                         if (!last) {
                             // queue the survivors of all 8 words for stage 1 at once (prefix
@@ -525,76 +623,115 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
                     }
                     have_pref = next_dense;
                 } else {
-                    uint32_t nz = __ballot_sync(FULL, wq != 0u && lane < (uint32_t)nw);
-                    while (nz) {
-                        const int j = __ffs(nz) - 1;
-                        nz &= nz - 1u;
-                        const uint32_t m = __shfl_sync(FULL, wq, j);
-                        const uint32_t q0 = qget(0);
-                        if ((m >> lane) & 1u) queue[q0 + __popc(m & lt_mask)] = sub_row0 + 32u * j + lane;
-                        qset(0, q0 + __popc(m));
+                    // Sparse sub-round: every lane appends the rows of its own word
+                    // (a warp prefix sum of the popcounts gives each lane its place),
+                    // when the queue has room for all of them; else one word at a time.
+                    const uint32_t c = __popc(wq);
+                    uint32_t incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= (uint32_t)o) incl += t;
+                    }
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t q0 = qget(0);
+                    if (q0 + total <= (uint32_t)kQueueCap) {
+                        uint32_t pos = q0 + incl - c;
+                        uint32_t m = wq;
+                        const uint32_t row = sub_row0 + 32u * lane;
+                        while (m) {
+                            queue[pos++] = row + (uint32_t)(__ffs(m) - 1);
+                            m &= m - 1u;
+                        }
+                        qset(0, q0 + total);
                         __syncwarp();
-                        if (q0 + __popc(m) >= (uint32_t)kDrain) {
+                        while (qget(0) >= (uint32_t)kDrain) {
                             run_stage(0, kDrain, round_row0);
                             cascade(0, round_row0);
+                        }
+                    } else {
+                        uint32_t nz = __ballot_sync(FULL, wq != 0u);
+                        while (nz) {
+                            const int j = __ffs(nz) - 1;
+                            nz &= nz - 1u;
+                            const uint32_t m = __shfl_sync(FULL, wq, j);
+                            const uint32_t qj = qget(0);
+                            if ((m >> lane) & 1u) queue[qj + __popc(m & lt_mask)] = sub_row0 + 32u * j + lane;
+                            qset(0, qj + __popc(m));
+                            __syncwarp();
+                            if (qj + __popc(m) >= (uint32_t)kDrain) {
+                                run_stage(0, kDrain, round_row0);
+                                cascade(0, round_row0);
+                            }
                         }
                     }
                 }
             }
-            // flush: every queued row of this round goes through its remaining stages
-            for (int s = 0; s < n_in; ++s) {
-                while (qget(s) > 0) {
-                    run_stage(s, min(qget(s), (uint32_t)kDrain), round_row0);
-                    cascade(s, round_row0);
-                }
-            }
+            // rows still queued stay queued (their survivors will be set in
+            // the output bitmap directly); store the round's survivor words
             __syncwarp();
-#pragma unroll
-            for (int q = 0; q < NS; ++q) ow[q] = obm[32 * q + lane];
-            for (int s = 0; s < n_in; ++s) {
-                const int32_t d0 = s_pe[s].col[0].dtype, d1 = s_pe[s].col[1].dtype;
-                const bool two = s_pe[s].ncols == 2;
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const uint32_t am = abm[s * kRoundWords + 32 * q + lane];
-                    psec += sectors_of(am, d0);
-                    if (two) psec += sectors_of(am, d1);
-                }
-            }
-            __syncwarp();
-        }
-        uint32_t pc = 0;
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const int64_t wl = rb + 32 * q + lane;
-            if (wl < w_end) a.out_bits[wl] = ow[q];
-            pc += __popc(ow[q]);
-        }
-        if (a.ids) {
-            for (int b = 0; b < a.n_bcols; ++b) {
-                const int32_t dt = a.bcol[b].dtype;
-#pragma unroll
-                for (int q = 0; q < NS; ++q) bsec += sectors_of(ow[q], dt);
-            }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                // only the words that hold survivors (words past the chunk are zero)
-                uint32_t nz = __ballot_sync(FULL, ow[q] != 0u);
-                while (nz) {
-                    const int j = __ffs(nz) - 1;
-                    nz &= nz - 1u;
-                    const uint32_t m = __shfl_sync(FULL, ow[q], j);
-                    if ((m >> lane) & 1u)
-                        a.ids[seg_pos + __popc(m & lt_mask)] = round_row0 + 1024u * q + 32u * j + lane;
-                    seg_pos += __popc(m);
-                }
+                const int64_t wl = rb + 32 * q + lane;
+                if (wl < w_end) a.out_bits[wl] = obm[32 * q + lane];
             }
+            __syncwarp();
         }
-        local += __reduce_add_sync(FULL, pc);
 #pragma unroll
         for (int q = 0; q < NS; ++q) win[q] = win_next[q];
     }
+    // the rows still queued go through their remaining stages
+    for (int s = 0; s < n_in; ++s) {
+        while (qget(s) > 0) {
+            run_stage(s, min(qget(s), (uint32_t)kDrain), kNoRow);
+            cascade(s, kNoRow);
+        }
+    }
+    __syncwarp();
 
+    // Compaction of the chunk's survivors from its finished output words
+    // (read past L1: some bits were set by atomics): lane l takes word l of
+    // each group of 32, a warp prefix sum of the popcounts places its rows.
+    uint32_t local = 0;  // per lane; reduced below
+    unsigned long long bsec = 0;
+    int64_t seg_pos = w_begin * 32;  // next free slot of this warp's id segment
+    constexpr int CB = 8;  // groups of 32 words loaded at once (independent loads in flight)
+    for (int64_t g0 = w_begin; g0 < w_end; g0 += 32 * CB) {
+        uint32_t owb[CB];
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            const int64_t wl = g0 + 32 * j + lane;
+            owb[j] = wl < w_end ? __ldcg(a.out_bits + wl) : 0u;
+        }
+#pragma unroll 1
+        for (int j = 0; j < CB; ++j) {
+        const int64_t g = g0 + 32 * j;
+        if (g >= w_end) break;
+        const int64_t wl = g + lane;
+        const uint32_t ow = owb[j];
+        const uint32_t c = __popc(ow);
+        local += c;
+        if (a.ids) {
+            for (int b = 0; b < a.n_bcols; ++b) bsec += sectors_of(ow, a.bcol[b].dtype);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= (uint32_t)o) incl += t;
+            }
+            uint32_t* dst = a.ids + seg_pos + (incl - c);
+            const uint32_t row = (uint32_t)(wl * 32);
+            uint32_t m = ow;
+            while (m) {
+                *dst++ = row + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+            }
+            seg_pos += __shfl_sync(FULL, incl, 31);
+        }
+        }
+    }
+
+    local = __reduce_add_sync(FULL, local);
     psec = __reduce_add_sync(FULL, (unsigned)psec);
     bsec = __reduce_add_sync(FULL, (unsigned)bsec);
     if (lane == 0) {
@@ -649,6 +786,156 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
         __syncthreads();
         scan_cta<B, KT>(s_a, f, (int64_t)task.part * C + rank, rank, smem, sh);
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 1a. first probe of a visit that starts with every row alive
+//
+// A visit with no input bitmap (a forward-pass visit of a table without a
+// local predicate) tests its first filter in probe order on every row, so
+// that stage is a plain stream over the edge's key column(s): no queue and
+// no compaction.  This kernel runs that stage alone with a small register
+// footprint -- four 256-thread CTAs per SM instead of the scan kernel's two
+// -- so that twice the warps cover the key loads and the filter reads.  It
+// writes the rows that pass as a bitmap; the scan kernel then runs the
+// remaining probes with that bitmap as its input (the probe order, and so
+// the sector accounting, is the same as in one kernel).
+//
+// Warp w takes tiles of 256 rows (8 bitmap words) w, w + W, w + 2W, ...
+// (W warps in the grid); lane l holds rows l + 32 i (i < 8) of a tile, so a
+// key load of the warp is one coalesced access of 32 rows and the tile's 8
+// survivor words are 8 ballots.  The keys of the warp's next tile are
+// loaded before the current tile is hashed.
+// ---------------------------------------------------------------------------
+template <int B, int KT>
+__global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
+    pt_probe_first_kernel(const VisitArgs a, const FilterCfg f, uint32_t* __restrict__ mid, int32_t* first,
+                          const int32_t smem_words) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ ProbeEdge s_pe;
+    __shared__ uint32_t s_nb;
+    __shared__ int32_t s_fit;
+    constexpr uint32_t WPB = B / 32;
+    constexpr int R = kFirstTileRows / 32;  // rows per lane of a tile
+    const uint32_t FULL = 0xFFFFFFFFu;
+    if (threadIdx.x == 0) {
+        int ord[kMaxIn];
+        lip_order(a, -1, ord);
+        s_pe = a.in[ord[0]];
+        s_nb = (uint32_t)*s_pe.nblocks;
+        s_fit = (int64_t)s_nb * WPB <= (int64_t)smem_words;
+        if (blockIdx.x == 0) *first = ord[0];
+    }
+    __syncthreads();
+    const uint32_t nb = s_nb;
+    const bool in_smem = s_fit != 0;
+    if (in_smem) {
+        const uint4* src = reinterpret_cast<const uint4*>(s_pe.filter);
+        uint4* dst = reinterpret_cast<uint4*>(smem);
+        for (uint32_t t = threadIdx.x; t < nb * (WPB / 4); t += blockDim.x) dst[t] = __ldg(src + t);
+    }
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t n = a.n;
+    const int64_t n_words = (n + 31) >> 5;
+    const int64_t n_tiles = (n + kFirstTileRows - 1) / kFirstTileRows;
+    const int64_t n_full = n / kFirstTileRows;  // tiles with every row inside the table
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const ColRef c0 = s_pe.col[0], c1 = s_pe.col[1];
+    const int ncols = s_pe.ncols;
+    const uint32_t* fg = s_pe.filter;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const int k = f.k;
+    const uint64_t seed = f.seed;
+
+    // the R rows of a lane, with the filter's location branched on once
+    auto probe = [&](const uint64_t* h, bool* pass) {
+        if (in_smem)
+            probe_shared_n<B, KT, R>(sbase, nb, h, k, pass);
+        else
+            probe_global_n<B, KT, R>(fg, nb, h, k, pass);
+    };
+    // the tile's survivor words: word i is ballot i; lanes 0..7 store one each
+    auto store = [&](int64_t t, const bool* pass) {
+        uint32_t myw = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const uint32_t m = __ballot_sync(FULL, pass[i]);
+            if (lane == (uint32_t)i) myw = m;
+        }
+        const int64_t w = t * R + lane;
+        if (lane < (uint32_t)R && w < n_words) mid[w] = myw;
+    };
+
+    if (ncols == 1 && c0.dtype != 0) {
+        // one 64-bit column (int64 keys, or precomputed hashes): keys prefetched a tile ahead
+        const long long* col = reinterpret_cast<const long long*>(c0.p);
+        const bool hashed = c0.dtype == kHashed;
+        auto load = [&](int64_t t, uint64_t* kv) {
+            const int64_t r0 = t * kFirstTileRows + lane;
+            if (t < n_full) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) kv[i] = (uint64_t)__ldg(col + r0 + 32 * i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) kv[i] = r0 + 32 * i < n ? (uint64_t)__ldg(col + r0 + 32 * i) : 0ull;
+            }
+        };
+        uint64_t kv[R];
+        if (gw < n_tiles) load(gw, kv);
+        for (int64_t t = gw; t < n_tiles; t += W) {
+            uint64_t h[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) h[i] = kv[i];
+            if (t + W < n_tiles) load(t + W, kv);
+            if (!hashed) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) h[i] = hash_key(h[i], seed);
+            }
+            bool pass[R];
+            probe(h, pass);
+            if (t >= n_full) {  // the ragged last tile: rows past the table do not pass
+                const int64_t r0 = t * kFirstTileRows + lane;
+#pragma unroll
+                for (int i = 0; i < R; ++i) pass[i] = pass[i] && r0 + 32 * i < n;
+            }
+            store(t, pass);
+        }
+    } else {
+        // int32 keys or a composite key: no prefetch
+        for (int64_t t = gw; t < n_tiles; t += W) {
+            const int64_t r0 = t * kFirstTileRows + lane;
+            uint64_t h[R];
+            bool live[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                live[i] = r0 + 32 * i < n;
+                h[i] = live[i] ? edge_hash(c0, c1, ncols, (uint32_t)(r0 + 32 * i), seed) : 0ull;
+            }
+            bool pass[R];
+            probe(h, pass);
+#pragma unroll
+            for (int i = 0; i < R; ++i) pass[i] = pass[i] && live[i];
+            store(t, pass);
+        }
+    }
+
+    // key sectors this stage read: every sector of the edge's column(s)
+    unsigned long long psec = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t tail = (uint32_t)(n & 31);
+        const uint32_t alive = (w == n_words - 1 && tail) ? (1u << tail) - 1u : FULL;
+        psec += sectors_of(alive, c0.dtype);
+        if (ncols == 2) psec += sectors_of(alive, c1.dtype);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) psec += __shfl_xor_sync(FULL, psec, o);
+    if (lane == 0 && psec) {
+        atomicAdd(a.stats + 0, psec);
+        atomicAdd(a.stats + 2, psec);
     }
 }
 
@@ -830,6 +1117,30 @@ cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int bl
     }
     if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<256, 4>, c, grid, block, smem, s, a, f);
     return launch_maybe_cluster(pt_scan_kernel<256, 0>, c, grid, block, smem, s, a, f);
+}
+
+cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t* mid, int32_t* first,
+                               int32_t smem_words, int grid, int block, size_t smem, cudaStream_t s) {
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_probe_first_kernel<512, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+        else pt_probe_first_kernel<512, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+    } else {
+        if (f.k == 4) pt_probe_first_kernel<256, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+        else pt_probe_first_kernel<256, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+    }
+    return cudaGetLastError();
+}
+
+int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem) {
+    int n = 0, m = 0;
+    if (block_bits == 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_probe_first_kernel<512, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_probe_first_kernel<512, 0>, block, smem);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_probe_first_kernel<256, 4>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_probe_first_kernel<256, 0>, block, smem);
+    }
+    return n < m ? n : m;
 }
 
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s) {

@@ -58,6 +58,10 @@ struct Visit {
     int64_t max_in_filter_bytes = 0;     // sum over incoming edges of the filters' largest sizes
     int64_t max_single_filter_bytes = 0; // the largest of them
     ScanShape shape;
+    // a first-probe pass (every row alive, large table): its launch shape
+    bool first = false;
+    int first_grid = 0;
+    size_t first_smem = 0;
 };
 
 }  // namespace
@@ -84,7 +88,10 @@ struct pt_ctx {
     std::vector<uint32_t*> filt[2];
     std::vector<int64_t> filt_max_words;
     unsigned long long* counts[2] = {nullptr, nullptr};  // [table]
-    unsigned long long* stats[2] = {nullptr, nullptr};   // [table][2]
+    unsigned long long* stats[2] = {nullptr, nullptr};   // [table][3]
+    int32_t* first_idx = nullptr;                        // [table]: edge the first-probe pass tested
+    std::vector<uint32_t*> mid;                          // [table]: its survivors, or nullptr
+    bool first_probe = true;                             // run first-probe passes where they apply
     int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
     void* meta[2] = {nullptr, nullptr};
     size_t meta_bytes = 0;
@@ -273,6 +280,10 @@ pt_status check_columns(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_co
 // Shared memory one scan CTA may use when two share an SM (228 KB per SM,
 // minus the kernel's static part).
 constexpr int64_t kScanCtaSmem = 112 * 1024;
+// Dynamic shared memory of a first-probe CTA: below the default 48 KB limit
+// (which also covers the kernel's static shared memory), so no kernel
+// attribute is needed; four such CTAs leave most of an SM's 228 KB to L1.
+constexpr int64_t kFirstCtaSmem = 46 * 1024;
 constexpr int kMaxCluster = 4;
 
 ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
@@ -322,7 +333,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     a.in_bits = p == 0 ? ctx->tables[v].sel : ctx->surv[0][v];
     a.out_bits = ctx->surv[p][v];
     a.count = ctx->counts[p] + v;
-    a.stats = ctx->stats[p] + 2 * v;
+    a.stats = ctx->stats[p] + 3 * v;
     a.n_in = (int)vis.in_edges.size();
     a.n_out = (int)vis.out_edges.size();
     a.words_per_warp = sh.words_per_warp;
@@ -379,6 +390,19 @@ pt_status prepare_shapes(pt_ctx* ctx) {
     }
     for (int p = 0; p < 2; ++p)
         for (Visit& vis : ctx->visits[p]) vis.shape = scan_shape(ctx, vis);
+    for (Visit& vis : ctx->visits[0]) {
+        if (!vis.first) continue;
+        // the filter budget of one CTA: the largest incoming filter, at most
+        // the context's budget (a first filter that does not fit is probed from L2)
+        const int64_t want = std::min<int64_t>(std::min<int64_t>(ctx->smem_budget, kFirstCtaSmem),
+                                               vis.max_single_filter_bytes);
+        vis.first_smem = (size_t)(want / 16 * 16);
+        int fit = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, vis.first_smem);
+        if (fit < 1) fit = 1;
+        const int64_t tiles = (ctx->tables[vis.table].n + pt::kFirstTileRows - 1) / pt::kFirstTileRows;
+        const int64_t want_ctas = (tiles + pt::kFirstThreads / 32 - 1) / (pt::kFirstThreads / 32);
+        vis.first_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit));
+    }
     ctx->shapes_ready = true;
     return PT_OK;
 }
@@ -419,6 +443,16 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         pt::VisitArgs a;
         fill_visit_args(ctx, p, vis, sh, a);
         pt_status s1;
+        if (p == 0 && vis.first && ctx->first_probe) {
+            if ((s1 = record_event(ctx, 2, st)) != PT_OK) return s1;
+            PT_CUDA(ctx, pt::launch_probe_first(a, ctx->fcfg, ctx->mid[v], ctx->first_idx + v,
+                                                (int32_t)(vis.first_smem / 4), vis.first_grid, pt::kFirstThreads,
+                                                vis.first_smem, st));
+            if ((s1 = record_event(ctx, 2, st)) != PT_OK) return s1;
+            ctx->launches++;
+            a.in_bits = ctx->mid[v];
+            a.first_in = ctx->first_idx + v;
+        }
         if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
         PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st));
         if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
@@ -617,6 +651,8 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                 (int)vis.bcols.size() > pt::kMaxBuildCols)
                 return fail(ctx, PT_ERR_UNSUPPORTED, "table %d has more than %d incoming or %d outgoing edges in a pass",
                             vis.table, pt::kMaxIn, pt::kMaxOut);
+            vis.first = p == 0 && !vis.in_edges.empty() && ctx->tables[vis.table].sel == nullptr &&
+                        ctx->tables[vis.table].n >= pt::kFirstMinRows;
             ctx->visits[p].push_back(vis);
         }
     }
@@ -649,7 +685,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     std::vector<bool> has_edge(T, false);
     for (int e = 0; e < E; ++e) has_edge[ctx->edges[e].t0] = has_edge[ctx->edges[e].t1] = true;
     size_t off = 0;
-    std::vector<size_t> o_surv[2], o_ids(T), o_seg(T), o_filt[2];
+    std::vector<size_t> o_surv[2], o_ids(T), o_seg(T), o_filt[2], o_mid(T, 0);
+    std::vector<bool> has_mid(T, false);
+    for (const Visit& vis : ctx->visits[0]) has_mid[vis.table] = vis.first;
     for (int p = 0; p < 2; ++p) {
         o_surv[p].resize(T);
         o_filt[p].resize(E);
@@ -664,13 +702,16 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         if (has_edge[v]) off += align_up(std::max<size_t>((size_t)n[v] * 4, 16));
         o_seg[v] = off;
         if (has_edge[v]) off += align_up((size_t)ctx->seg_cap * 4);
+        o_mid[v] = off;
+        if (has_mid[v]) off += align_up(std::max<size_t>(wb, 16));
     }
     for (int e = 0; e < E; ++e)
         for (int p = 0; p < 2; ++p) {
             o_filt[p][e] = off;
             off += align_up((size_t)ctx->filt_max_words[e] * 4);
         }
-    ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 16 + (size_t)std::max(E, 1) * 8);
+    // counts [T] u64, stats [T][3] u64, nblocks [E] i64, first-probe edge [T] i32
+    ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 24 + (size_t)std::max(E, 1) * 8 + (size_t)T * 4);
     size_t o_meta[2];
     for (int p = 0; p < 2; ++p) {
         o_meta[p] = off;
@@ -694,8 +735,12 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         ctx->meta[p] = base + o_meta[p];
         ctx->counts[p] = (unsigned long long*)(base + o_meta[p]);
         ctx->stats[p] = (unsigned long long*)(base + o_meta[p] + (size_t)T * 8);
-        ctx->nblocks[p] = (int64_t*)(base + o_meta[p] + (size_t)T * 24);
+        ctx->nblocks[p] = (int64_t*)(base + o_meta[p] + (size_t)T * 32);
     }
+    ctx->first_idx = (int32_t*)(base + o_meta[0] + (size_t)T * 32 + (size_t)std::max(E, 1) * 8);
+    ctx->mid.assign(T, nullptr);
+    for (int v = 0; v < T; ++v)
+        if (has_mid[v]) ctx->mid[v] = (uint32_t*)(base + o_mid[v]);
     ctx->ids.resize(T);
     ctx->seg.resize(T);
     for (int v = 0; v < T; ++v) {
@@ -837,10 +882,10 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
     if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
     const int T = (int)ctx->tables.size(), E = (int)ctx->edges.size();
-    std::vector<unsigned long long> c(T), s(2 * T);
+    std::vector<unsigned long long> c(T), s(3 * T);
     std::vector<int64_t> nb(std::max(E, 1));
     PT_CUDA(ctx, cudaMemcpyAsync(c.data(), ctx->counts[pass], T * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    PT_CUDA(ctx, cudaMemcpyAsync(s.data(), ctx->stats[pass], 2 * T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaMemcpyAsync(s.data(), ctx->stats[pass], 3 * T * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (E) PT_CUDA(ctx, cudaMemcpyAsync(nb.data(), ctx->nblocks[pass], E * 8, cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const Visit* vis = nullptr;
@@ -849,12 +894,25 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     std::memset(out, 0, sizeof *out);
     out->n_rows = ctx->tables[table_id].n;
     out->survivors = (int64_t)c[table_id];
-    out->probe_sectors = (int64_t)s[2 * table_id];
-    out->build_sectors = (int64_t)s[2 * table_id + 1];
+    out->probe_sectors = (int64_t)s[3 * table_id];
+    out->build_sectors = (int64_t)s[3 * table_id + 1];
+    out->first_probe_sectors = (int64_t)s[3 * table_id + 2];
+    out->first_probe = out->first_probe_sectors > 0 ? 1 : 0;
     out->n_in = (int32_t)vis->in_edges.size();
     out->n_out = (int32_t)vis->out_edges.size();
     for (int e : vis->out_edges) out->filter_bytes += nb[e] * ctx->fcfg.block_bits / 8;
     out->has_input_bitmap = pass == 1 || ctx->tables[table_id].sel != nullptr;
+    return PT_OK;
+}
+
+pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (enable != 0 && enable != 1) return fail(ctx, PT_ERR_INVALID, "enable must be 0 or 1 (got %d)", enable);
+    if (ctx->first_probe != (enable == 1) && ctx->gexec) {  // the captured launch sequence changes
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->first_probe = enable == 1;
     return PT_OK;
 }
 
@@ -896,12 +954,10 @@ pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on) {
     return PT_OK;
 }
 
-pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
-                             int32_t* other_launches) {
-    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+namespace {
+// Summed event times of kind 0 (scan), 1 (size/clear + insert), 2 (first probe).
+pt_status kernel_times(pt_ctx* ctx, double* t, int* n) {
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    double t[3] = {0, 0, 0};
-    int n[3] = {0, 0, 0};
     auto sum = [&](const std::vector<cudaEvent_t>& ev, const std::vector<int>& kinds, size_t used) -> pt_status {
         for (size_t i = 0; i + 1 < used; i += 2) {
             float ms = 0.f;
@@ -917,10 +973,37 @@ pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launche
         st = sum(ctx->gev, ctx->gev_kind, ctx->gev_used);  // the most recent replay
         if (st != PT_OK) return st;
     }
-    if (scan_ms) *scan_ms = t[0];
-    if (scan_launches) *scan_launches = n[0];
-    if (other_ms) *other_ms = t[1] + t[2];
-    if (other_launches) *other_launches = n[1] + n[2];
+    return PT_OK;
+}
+}  // namespace
+
+pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
+                             int32_t* other_launches) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    double t[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+    pt_status st = kernel_times(ctx, t, n);
+    if (st != PT_OK) return st;
+    if (scan_ms) *scan_ms = t[0] + t[2];
+    if (scan_launches) *scan_launches = n[0] + n[2];
+    if (other_ms) *other_ms = t[1];
+    if (other_launches) *other_launches = n[1];
+    return PT_OK;
+}
+
+pt_status pt_get_kernel_times(pt_ctx* ctx, pt_kernel_times* out) {
+    if (!ctx || !out) return fail(ctx, PT_ERR_INVALID, "ctx or out is NULL");
+    double t[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+    pt_status st = kernel_times(ctx, t, n);
+    if (st != PT_OK) return st;
+    std::memset(out, 0, sizeof *out);
+    out->first_ms = t[2];
+    out->scan_ms = t[0];
+    out->build_ms = t[1];
+    out->first_launches = n[2];
+    out->scan_launches = n[0];
+    out->build_pairs = n[1];
     return PT_OK;
 }
 

@@ -47,7 +47,14 @@ class pt_edge(C.Structure):
 class pt_visit_stats(C.Structure):
     _fields_ = [("n_rows", C.c_int64), ("survivors", C.c_int64), ("probe_sectors", C.c_int64),
                 ("build_sectors", C.c_int64), ("filter_bytes", C.c_int64), ("n_in", C.c_int32),
-                ("n_out", C.c_int32), ("has_input_bitmap", C.c_int32), ("reserved", C.c_int32)]
+                ("n_out", C.c_int32), ("has_input_bitmap", C.c_int32), ("first_probe", C.c_int32),
+                ("first_probe_sectors", C.c_int64)]
+
+
+class pt_kernel_times(C.Structure):
+    _fields_ = [("first_ms", C.c_double), ("scan_ms", C.c_double), ("build_ms", C.c_double),
+                ("first_launches", C.c_int32), ("scan_launches", C.c_int32), ("build_pairs", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pt_static_probe(C.Structure):
@@ -89,6 +96,8 @@ _SIGS = {
     "pt_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "pt_set_kernel_timing": (C.c_int, [_P, C.c_int32]),
     "pt_set_cluster": (C.c_int, [_P, C.c_int32]),
+    "pt_set_first_probe": (C.c_int, [_P, C.c_int32]),
+    "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
     "pt_get_kernel_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "pt_get_launch_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
@@ -252,6 +261,16 @@ def pt_get_kernel_time(ctx: int) -> dict:
            "pt_get_kernel_time", ctx)
     return {"scan_ms": sm.value, "scan_launches": sn.value, "other_ms": om.value,
             "other_launches": on.value}
+
+
+def pt_get_kernel_times(ctx: int) -> dict:
+    t = pt_kernel_times()
+    _check(lib.pt_get_kernel_times(ctx, C.byref(t)), "pt_get_kernel_times", ctx)
+    return {f: getattr(t, f) for f, _ in pt_kernel_times._fields_ if f != "reserved"}
+
+
+def pt_set_first_probe(ctx: int, enable: bool) -> None:
+    _check(lib.pt_set_first_probe(ctx, int(enable)), "pt_set_first_probe", ctx)
 
 
 def pt_get_launch_count(ctx: int) -> int:

@@ -25,9 +25,9 @@ def edges_of(w):
     return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1)) for e in w.edges]
 
 
-def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None):
+def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None, first_probe=None):
     return TransferSession(device_tables(w, host, pin), edges_of(w), w.bits_per_key, w.k, w.block_bits,
-                           w.seed, launch=launch, graph=graph, cluster=cluster)
+                           w.seed, launch=launch, graph=graph, cluster=cluster, first_probe=first_probe)
 
 
 def collect(s, w):
@@ -42,6 +42,8 @@ def collect(s, w):
             out["count"][p][v] = c
             st = s.stats(p, v)
             out["sectors"][p][v] = (st["probe_sectors"], st["build_sectors"])
+            out.setdefault("first", [[None] * nt for _ in range(2)])[p][v] = (st["first_probe"],
+                                                                              st["first_probe_sectors"])
         for e in range(ne):
             f = s.filter(p, e).cpu().numpy().view(np.uint32)
             out["filters"][p][e] = f

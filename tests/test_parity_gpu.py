@@ -95,6 +95,28 @@ def test_empty_and_full_selections(oracle_lib):
     _check(w, oracle_lib)
 
 
+def test_mixed_dense_and_sparse_input_runs(oracle_lib):
+    # the fact table's selection alternates all-ones runs (dense sub-rounds of
+    # the scan) with sparse stretches, so queued rows and dense rows meet in
+    # the same stages; survivors and sector counts must still equal the oracle's
+    rng = np.random.default_rng(77)
+    n = 400_000 + 13
+    dims = []
+    for nd, frac in ((3000, 0.2), (50_000, 0.5), (700, 0.9)):
+        d = rng.permutation(nd).astype(np.int64) * 3 + 5
+        dims.append(W.Table(f"D{nd}", nd, [d], ["id"], W.bitmap_from_bools(rng.random(nd) < frac)))
+    cols = [d.cols[0][rng.integers(0, d.n_rows, n)] for d in dims]
+    keep = np.zeros(n, bool)
+    for start in range(0, n, 9000):
+        if (start // 9000) % 2 == 0:
+            keep[start:start + 5000] = True                       # runs of whole words
+        else:
+            keep[start:start + 9000] = rng.random(min(9000, n - start)) < 0.05
+    F = W.Table("F", n, cols, ["a", "b", "c"], W.bitmap_from_bools(keep))
+    w = W.Workload("mixed", [F] + dims, [W.Edge(0, (i,), i + 1, (0,)) for i in range(3)], 16, 4, 256, 0)
+    _check(w, oracle_lib)
+
+
 def test_graph_mode_host_columns_and_repeat(oracle_lib):
     from _gpu import assert_same, collect, session_for
     w = W.snowflake(scale=0.02, int64=True, composite=True, bits_per_key=10)
