@@ -37,10 +37,12 @@
  *           table on the other end of the edge.
  *   order:  tables are ranked by (rows, table id); the forward pass visits
  *           them in ascending rank, the backward pass in descending rank.
- *   probe:  incoming filters are probed in ascending c_b / n_b (survivors
- *           of the building visit over its table's rows), ties by edge id
- *           (LIP-style ordering, Section 3.2); the order never changes a
- *           result, only how many key sectors are read.
+ *   probe:  incoming filters are probed in ascending level of the building
+ *           visit (its longest path from a source of the pass's DAG, so
+ *           filters that are finished earlier come first), then ascending
+ *           c_b / n_b (survivors of the building visit over its table's
+ *           rows, the LIP-style ordering of Section 3.2), then edge id; the
+ *           order never changes a result, only how many key sectors are read.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -229,6 +231,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
     int32_t* ine = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
     o_pair** set = (o_pair**)calloc((size_t)(2 * n_edges + 1), sizeof(o_pair*));
     int64_t* set_n = (int64_t*)calloc((size_t)(2 * n_edges + 1), sizeof(int64_t));
+    int32_t* lvl = (int32_t*)calloc((size_t)(2 * n_tables + 1), sizeof(int32_t));
 
     for (v = 0; v < n_tables; v++) n_rows[v] = t[v].n_rows;
     o_orient(n_tables, n_rows, n_edges, e, src, dst, order);
@@ -245,21 +248,29 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
 
             for (int64_t r = 0; r < n; r++) alive[r] = in ? (unsigned char)o_bit(in, r) : 1;
 
-            /* incoming edges of v in this pass, in LIP order */
-            int32_t n_in = 0;
+            /* incoming edges of v in this pass; v's level is one more than
+               its highest builder's (builders are visited before v) */
+            int32_t n_in = 0, lv = 0;
             for (i = 0; i < n_edges; i++) {
                 int32_t into = p == 0 ? dst[i] : src[i];
-                if (into == v) ine[n_in++] = i;
+                if (into == v) {
+                    int32_t b = p == 0 ? src[i] : dst[i];
+                    ine[n_in++] = i;
+                    if (lvl[p * n_tables + b] + 1 > lv) lv = lvl[p * n_tables + b] + 1;
+                }
             }
+            lvl[p * n_tables + v] = lv;
+            /* probe order: builder level, then LIP ratio, then edge id */
             for (i = 1; i < n_in; i++) {
                 int32_t x = ine[i];
                 j = i - 1;
                 while (j >= 0) {
                     int32_t y = ine[j];
                     int32_t bx = p == 0 ? src[x] : dst[x], by = p == 0 ? src[y] : dst[y];
+                    int32_t lx = lvl[p * n_tables + bx], ly = lvl[p * n_tables + by];
                     uint64_t lhs = (uint64_t)count[p * n_tables + bx] * (uint64_t)n_rows[by];
                     uint64_t rhs = (uint64_t)count[p * n_tables + by] * (uint64_t)n_rows[bx];
-                    if (lhs < rhs || (lhs == rhs && x < y)) { ine[j + 1] = ine[j]; j--; }
+                    if (lx < ly || (lx == ly && (lhs < rhs || (lhs == rhs && x < y)))) { ine[j + 1] = ine[j]; j--; }
                     else break;
                 }
                 ine[j + 1] = x;
@@ -337,6 +348,6 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
         }
     }
     for (i = 0; i < 2 * n_edges; i++) free(set[i]);
-    free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(ine);
+    free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(ine); free(lvl);
     return 0;
 }

@@ -12,7 +12,7 @@ constexpr int kMaxOut = 8;        // outgoing edges of one visit
 constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
 constexpr int kRoundWords = 128;  // bitmap words (32 rows each) a scan warp takes per round
 constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words
-constexpr int kDrain = 64;        // a probe stage runs once its queue holds this many rows
+constexpr int kDrain = 128;       // a probe stage runs once its queue holds this many rows
 constexpr int kQueueCap = kDrain + 256;  // row-id queue in front of a probe stage (per warp): room for
                                          // a drain's worth plus 8 dense words (256 rows) or a sparse sub-round
 constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
@@ -55,6 +55,8 @@ struct ProbeEdge {
     const int64_t* nblocks;                   // written by the builder's size/clear kernel
     const unsigned long long* build_count;    // survivors of the building visit
     int64_t build_rows;                       // rows of the building table
+    int32_t build_level;                      // the building visit's level in this pass's DAG
+    int32_t pad;
 };
 
 // An outgoing edge: the visit's key column(s) and the filter it builds.

@@ -251,9 +251,13 @@ struct ScanShared {
     int32_t n_in;            // edges this kernel probes (a first-probe pass may have taken one)
 };
 
-// Probe order (LIP-style): incoming edges by ascending survivors/rows of the
-// building visit, ties by edge id, with in[skip] left out (skip < 0: none).
-// Writes the in[] indexes to ord and returns their number.  One thread.
+// Probe order: incoming edges by ascending level of the building visit (its
+// longest path from a source of the pass's DAG: filters finished earlier come
+// first), then ascending survivors/rows of the building visit (LIP-style),
+// then edge id, with in[skip] left out (skip < 0: none).  Writes the in[]
+// indexes to ord and returns their number.  One thread.  The first edge
+// depends only on the counts of the lowest-level builders, so it can be taken
+// while higher-level builders still run.
 __device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord) {
     unsigned long long c[kMaxIn];
     int m = 0;
@@ -267,9 +271,10 @@ __device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord)
         int j = i - 1;
         while (j >= 0) {
             const int y = ord[j];
+            const int32_t lx = a.in[x].build_level, ly = a.in[y].build_level;
             const unsigned long long lhs = c[x] * (unsigned long long)a.in[y].build_rows;
             const unsigned long long rhs = c[y] * (unsigned long long)a.in[x].build_rows;
-            if (lhs < rhs || (lhs == rhs && a.in[x].edge_id < a.in[y].edge_id)) {
+            if (lx < ly || (lx == ly && (lhs < rhs || (lhs == rhs && a.in[x].edge_id < a.in[y].edge_id)))) {
                 ord[j + 1] = ord[j];
                 --j;
             } else {
@@ -1000,12 +1005,16 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
     const size_t seg_rows = (size_t)a.words_per_warp * 32;
     const int k = f.k;
     const uint64_t seed = f.seed;
+    // with more warps than segments, the ways-th part of every segment's
+    // batches goes to a different warp (more gathers in flight)
+    const int64_t ways = max((int64_t)1, n_warps / a.total_warps);
 
-    for (int64_t s = gw; s < a.total_warps; s += n_warps) {
+    for (int64_t t = gw; t < a.total_warps * ways; t += n_warps) {
+        const int64_t s = t % a.total_warps;
         const uint32_t cnt = a.seg_count[s];
         const uint32_t* ids = a.ids + (size_t)s * seg_rows;
         // four survivors per lane at a time: four independent key gathers in flight
-        for (uint32_t base = 0; base < cnt; base += 128) {
+        for (uint32_t base = 128u * (uint32_t)(t / a.total_warps); base < cnt; base += 128u * (uint32_t)ways) {
             uint32_t r[4];
             bool live[4];
 #pragma unroll

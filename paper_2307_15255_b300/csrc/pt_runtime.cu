@@ -133,6 +133,12 @@ struct pt_ctx {
     std::vector<cudaEvent_t> vev[2];  // per pass, per table: the visit's work is done
     cudaEvent_t pass_ev[2] = {nullptr, nullptr};
     std::vector<int> slot[2];         // per pass, per table: position inside its level
+    std::vector<int32_t> lvl[2];      // per pass, per table: level (longest path from a source)
+    // A first-probe pass runs on a stream of its own, as soon as the filters
+    // of its visit's lowest-level builders exist (it probes one of those),
+    // concurrently with the builders of the visit's other filters.
+    std::vector<cudaStream_t> fstream;  // per table with a first-probe pass, else nullptr
+    std::vector<cudaEvent_t> fev;       // its pass is done
 };
 
 namespace {
@@ -354,6 +360,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         pe.nblocks = ctx->nblocks[p] + e;
         pe.build_count = ctx->counts[p] + b;
         pe.build_rows = ctx->tables[b].n;
+        pe.build_level = ctx->lvl[p][b];
     }
     for (int i = 0; i < a.n_out; ++i) {
         const int e = vis.out_edges[i];
@@ -444,11 +451,21 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         fill_visit_args(ctx, p, vis, sh, a);
         pt_status s1;
         if (p == 0 && vis.first && ctx->first_probe) {
-            if ((s1 = record_event(ctx, 2, st)) != PT_OK) return s1;
+            // the first probe tests a filter of one of the lowest-level builders:
+            // it waits for those only, on its own stream
+            cudaStream_t fs = ctx->fstream[v];
+            PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
+            int32_t lmin = INT32_MAX;
+            for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->src[e]]);
+            for (int e : vis.in_edges)
+                if (ctx->lvl[p][ctx->src[e]] == lmin) PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->src[e]], 0));
+            if ((s1 = record_event(ctx, 2, fs)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_probe_first(a, ctx->fcfg, ctx->mid[v], ctx->first_idx + v,
                                                 (int32_t)(vis.first_smem / 4), vis.first_grid, pt::kFirstThreads,
-                                                vis.first_smem, st));
-            if ((s1 = record_event(ctx, 2, st)) != PT_OK) return s1;
+                                                vis.first_smem, fs));
+            if ((s1 = record_event(ctx, 2, fs)) != PT_OK) return s1;
+            PT_CUDA(ctx, cudaEventRecord(ctx->fev[v], fs));
+            PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fev[v], 0));
             ctx->launches++;
             a.in_bits = ctx->mid[v];
             a.first_in = ctx->first_idx + v;
@@ -464,7 +481,9 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
             int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
             if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
-            const int grid_i = std::max(1, std::min(sh.total_warps / 16 + 1, ctx->num_sms * 4));
+            // up to three 512-thread CTAs per SM; segments are split between warps when
+            // there are more warps than segments
+            const int grid_i = std::max(1, std::min(3 * sh.total_warps / 16 + 1, ctx->num_sms * 3));
             PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, st));
             if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
             ctx->launches += 2;
@@ -547,6 +566,10 @@ pt_status pt_destroy(pt_ctx* ctx) {
     }
     for (int i = 0; i < pt_ctx::kAux; ++i)
         if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
+    for (cudaStream_t f : ctx->fstream)
+        if (f) cudaStreamDestroy(f);
+    for (cudaEvent_t e : ctx->fev)
+        if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PT_OK;
@@ -666,7 +689,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         if (!ctx->pass_ev[p]) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pass_ev[p], cudaEventDisableTiming));
         ctx->vev[p].assign(T, nullptr);
         for (int v = 0; v < T; ++v) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->vev[p][v], cudaEventDisableTiming));
-        std::vector<int> lvl(T, 0), used;
+        std::vector<int> used;
+        std::vector<int32_t>& lvl = ctx->lvl[p];
+        lvl.assign(T, 0);
         for (const Visit& vis : ctx->visits[p])
             for (int e : vis.out_edges) {
                 const int to = p == 0 ? ctx->dst[e] : ctx->src[e];
@@ -678,6 +703,13 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             if ((int)used.size() <= l) used.resize(l + 1, 0);
             ctx->slot[p][vis.table] = used[l]++;
         }
+    }
+    ctx->fstream.assign(T, nullptr);
+    ctx->fev.assign(T, nullptr);
+    for (const Visit& vis : ctx->visits[0]) {
+        if (!vis.first) continue;
+        PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->fstream[vis.table], cudaStreamNonBlocking));
+        PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fev[vis.table], cudaEventDisableTiming));
     }
 
     // one device allocation holds every buffer of a run

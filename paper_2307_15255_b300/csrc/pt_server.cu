@@ -134,6 +134,7 @@ struct Query {
     int32_t src[kMaxQEdges] = {}, dst[kMaxQEdges] = {};
     std::vector<QVisit> visits[2];
     int levels[2] = {0, 0};
+    int lvl[2][kMaxInst] = {};  // per pass, per instance: level of its visit
     // device layout (offsets inside the query's arena allocation)
     size_t bytes = 0, base = 0;
     size_t o_surv[2][kMaxInst] = {}, o_ids[kMaxInst] = {}, o_seg[kMaxInst] = {}, o_sel[kMaxInst] = {};
@@ -266,6 +267,7 @@ pt_status plan_query(pt_server* S, Query* q) {
                 vis.level = std::max(vis.level, lvl[b] + 1);
             }
             lvl[vis.inst] = vis.level;
+            q->lvl[p][vis.inst] = vis.level;
             // scan tasks: tiles of kTileWords words, each run by a cluster of kCluster CTAs
             const int64_t words = (n[vis.inst] + 31) / 32;
             vis.grid = std::max<int64_t>(1, (words + kTileWords - 1) / kTileWords);
@@ -360,6 +362,7 @@ void fill_args(pt_server* S, const Query* q, int p, const QVisit& vis, unsigned 
         pe.nblocks = nblocks + e;
         pe.build_count = counts + b;
         pe.build_rows = S->tables[q->table[b]].n;
+        pe.build_level = q->lvl[p][b];
     }
     for (int i = 0; i < a.n_out; ++i) {
         const int e = vis.out_edges[i];

@@ -71,7 +71,6 @@ def _check_first(w, got, v, expect):
     dict(int64=True, composite=True, zipf=1.1, bits_per_key=16),  # int64, prefetched, smem filter
     dict(int64=False, bits_per_key=10),                             # int32 keys
     dict(int64=True, bits_per_key=10, k=7, block_bits=512),         # k read at run time, 512-bit blocks
-    dict(int64=True, composite=True, sel=(0.001, 0.5, 0.9)),        # the composite F->M key probes first
 ])
 def test_snowflake_fact_first_probe(oracle_lib, kw):
     w = W.snowflake(scale=0.25, **kw)  # fact 1.5M rows: 96 rows in its last tile
@@ -80,10 +79,26 @@ def test_snowflake_fact_first_probe(oracle_lib, kw):
     _check_first(w, got, 0, True)
     for v in range(1, w.n_tables):  # smaller tables, or tables with a selection
         _check_first(w, got, v, False)
-    if "sel" in kw:
-        # the F->M filter was the most selective: its two columns were the pass's sectors
-        f = w.tables[0]
-        assert got["first"][0][0][1] == 2 * _col_sectors(f.n_rows, np.int64)
+
+
+def test_composite_key_probed_first(oracle_lib):
+    # both builders are sources (level 0); the composite-key one keeps 1% of
+    # its rows, the other 50%, so the composite key is the first probe
+    rng = np.random.default_rng(21)
+    n = MIN_ROWS + 333
+    nm, nd = 20_000, 3000
+    m1 = rng.permutation(nm).astype(np.int64) * 5 + 1
+    m2 = rng.integers(-4, 4, nm).astype(np.int64)
+    d = rng.permutation(nd).astype(np.int64) - 1500
+    M = W.Table("M", nm, [m1, m2], ["k1", "k2"], W.bitmap_from_bools(rng.random(nm) < 0.01))
+    D = W.Table("D", nd, [d], ["id"], W.bitmap_from_bools(rng.random(nd) < 0.5))
+    rm, rd = rng.integers(0, nm, n), rng.integers(0, nd, n)
+    F = W.Table("F", n, [m1[rm], m2[rm], d[rd]], ["fk_m1", "fk_m2", "fk_d"], None)
+    w = W.Workload("composite_first", [F, M, D], [W.Edge(0, (0, 1), 1, (0, 1)), W.Edge(0, (2,), 2, (0,))],
+                   16, 4, 256, 0)
+    got = _run(w, oracle_lib)
+    _check_first(w, got, 0, True)
+    assert got["first"][0][0][1] == 2 * _col_sectors(n, np.int64)
 
 
 @pytest.mark.parametrize("smem", [0, 64 * 1024, 220 * 1024])

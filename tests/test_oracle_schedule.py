@@ -158,6 +158,33 @@ def test_lip_probe_order_sectors(oracle_lib):
     assert W.rows_from_bitmap(res["surv"][0][2], 64).tolist() == list(range(8))
 
 
+def test_probe_order_is_builder_level_first(oracle_lib):
+    """A less selective filter from a lower DAG level is probed first.
+
+    Ranks: B0 (4 rows) < A (8) < B1 (16) < V (64); edges A->V, B0->B1, B1->V,
+    so in the forward pass A and B0 are on level 0, B1 on level 1, V on 2.
+    A keeps rows 0..3 (keys 0..3, rate 4/8); B0 keeps key 0, so B1 keeps its
+    rows 0, 4, 8, 12 (rate 4/16).  LIP alone would probe B1's filter first;
+    the builder level puts A's first.  V.k_a = row // 8 passes A for rows
+    0..31, read over all 8 sectors of V.k_a (int32: 8 rows per sector); then
+    V.k_b = row % 16 is probed on rows 0..31 only: 4 sectors.  Total 12
+    (LIP alone would read 8 + 8 = 16).  Survivors: rows 0..31 with
+    row % 4 == 0.  Exact sets, so no false positives blur the count.
+    """
+    B0 = W.Table("B0", 4, [np.arange(4, dtype=np.int32)], ["k"], W.bitmap_from_rows(4, [0]))
+    A = W.Table("A", 8, [np.arange(8, dtype=np.int32)], ["k"], W.bitmap_from_rows(8, [0, 1, 2, 3]))
+    i16 = np.arange(16, dtype=np.int32)
+    B1 = W.Table("B1", 16, [i16 % 4, i16], ["b0", "bv"], None)
+    i64 = np.arange(64, dtype=np.int32)
+    V = W.Table("V", 64, [i64 // 8, i64 % 16], ["k_a", "k_b"], None)
+    w = W.Workload("levels", [B0, A, B1, V],
+                   [W.Edge(1, (0,), 3, (0,)), W.Edge(0, (0,), 2, (0,)), W.Edge(2, (1,), 3, (1,))])
+    res = oracle_lib.transfer(w, exact=True)
+    assert res["count"][0][2] == 4
+    assert res["sectors"][0][3] == (8 + 4, 0)
+    assert W.rows_from_bitmap(res["surv"][0][3], 64).tolist() == list(range(0, 32, 4))
+
+
 def test_chain3_exact_magnitudes(oracle_lib):
     """Expected sizes of the 3-table chain (10k/100k/10k, 10% and 20% kept):
     S keeps ~100k*0.1*0.2 = 2000 rows; R keeps ~1000*(1-e^-2) ~ 865 and T
