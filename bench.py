@@ -344,7 +344,7 @@ def kernel_source_hash() -> str:
 def committed_traffic(kernel: str, workload: str, bpk: int):
     """Per-launch DRAM bytes of `kernel` from a committed ncu summary, or
     None when none exists for the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "scan_kernel_traffic.json")
+    p = os.path.join(ROOT, "profiles", "probe_kernels_traffic.json")
     if not os.path.exists(p):
         return None
     try:
@@ -482,12 +482,20 @@ def ours(args) -> None:
     launches = P.pt_get_launch_count(s.ctx) - launches0
 
     # per-kernel times: the same graph recaptured with CUDA events around every
-    # scan launch (event-record nodes on the launching stream), replayed the
-    # same way; the events hold the last replay's durations
+    # launch (event-record nodes on the launching stream) and every launch on one
+    # stream, so that each kernel is timed alone; the events hold the last
+    # replay's durations
+    P.pt_set_streams(s.ctx, 1)
     P.pt_set_kernel_timing(s.ctx, True)
     for _ in range(max(args.warmup, 0) + args.steps):
         s.run()
     kt = P.pt_get_kernel_times(s.ctx)
+    # the concurrent step's last replay, launch by launch: [pass, table, kind, start ms, ms]
+    P.pt_set_streams(s.ctx, 3)
+    for _ in range(max(args.warmup, 0) + 1):
+        s.run()
+    timeline = [[x["pass"], w.tables[x["table"]].name, x["kind"], round(x["start_ms"], 4), round(x["ms"], 4)]
+                for x in P.pt_get_launch_times(s.ctx)]
     P.pt_set_kernel_timing(s.ctx, False)
     P.pt_set_graph_mode(s.ctx, False)
 
@@ -545,6 +553,8 @@ def ours(args) -> None:
         per_ms = kms / nl
         ach = (nbytes / nl) / (per_ms * 1e-3) / 1e9
         kernels.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        "launches_of": ("pt_scan_kernel and pt_scan_sparse_kernel (visits with an input bitmap)"
+                                        if name == "pt_scan_kernel" else name),
                         "frac": ach / peak, "peak_kind": peak_kind,
                         "traffic": committed_traffic(name, args.workload, args.bpk),
                         "alg_bytes_per_launch": nbytes / nl, "ms_per_launch": per_ms, "launches_timed": nl,
@@ -569,6 +579,7 @@ def ours(args) -> None:
         "roofline": roof,
         "roofline_kernels": kernels,
         "build_ms_per_step": kt["build_ms"],
+        "launch_timeline": timeline,
         "mode": "CUDA graph replay (direct launches: see direct_ms_per_step)",
         "direct_ms_per_step": direct_ms,
         "cpu_baseline": cpu,

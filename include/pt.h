@@ -216,6 +216,13 @@ pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
  * keeps every probe in the scan kernel.  Takes effect at the next run. */
 pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable);
 
+/* Streams the visits of one DAG level are spread over: 1..3 (default 3,
+ * visits of a level and a first-probe pass beside its visit's builders run
+ * concurrently).  1 runs every launch one after another on one stream, so
+ * that kernel timing (pt_set_kernel_timing) measures each kernel alone.
+ * Results do not depend on it.  Takes effect at the next run. */
+pt_status pt_set_streams(pt_ctx* ctx, int32_t streams);
+
 /* Kernel timing.  pt_set_kernel_timing(ctx, 1) records CUDA events around
  * every first-probe launch, every scan (probe + compact) launch and every
  * visit's size/clear + insert pair, on the stream each runs on.  Direct
@@ -239,6 +246,23 @@ pt_status pt_set_kernel_timing(pt_ctx* ctx, int32_t on);
 pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launches, double* other_ms,
                              int32_t* other_launches);
 pt_status pt_get_kernel_times(pt_ctx* ctx, pt_kernel_times* out);
+
+/* The same events one launch at a time, in the order they were enqueued:
+ * kind (0 scan, 1 size/clear + insert pair, 2 first probe), the pass and
+ * the table of the visit, the start relative to the first timed launch
+ * and the duration, both in milliseconds.  With graph mode on, the last
+ * replay's; else every direct launch since timing was switched on.  Writes
+ * at most max entries and sets *n to the number there are.  Synchronizes
+ * the context's stream. */
+typedef struct {
+    int32_t kind;
+    int32_t pass;
+    int32_t table;
+    int32_t reserved;
+    double start_ms;
+    double ms;
+} pt_launch_time;
+pt_status pt_get_launch_times(pt_ctx* ctx, int32_t max, pt_launch_time* out, int32_t* n);
 
 /* Number of kernels the library launched since the context was created
  * (a graph replay counts each of its kernel nodes). */

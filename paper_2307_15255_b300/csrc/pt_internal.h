@@ -17,6 +17,7 @@ constexpr int kQueueCap = kDrain + 256;  // row-id queue in front of a probe sta
                                          // a drain's worth plus 8 dense words (256 rows) or a sparse sub-round
 constexpr int kScanMaxThreads = 256;  // scan CTA size limit (launch bounds)
 constexpr int kScanMinBlocks = 2;     // scan CTAs per SM the register budget allows
+constexpr int kScanSparseMinBlocks = 3;  // the same for the scan of a visit with an input bitmap
 constexpr int kFirstThreads = 256;    // first-probe CTA size (launch bounds)
 constexpr int kFirstMinBlocks = 3;    // first-probe CTAs per SM the register budget allows
 constexpr int kFirstTileRows = 256;   // rows a first-probe warp takes at a time (8 bitmap words)
@@ -141,8 +142,9 @@ cudaError_t scan_batch_set_smem_limit(int block_bits, size_t smem);
 // Message returned by pt_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);
 
-// CTAs of the scan kernel that fit on one SM for this shape.
-int scan_max_ctas_per_sm(int block_bits, int block, size_t smem);
+// CTAs of the scan kernel (sparse: the one for visits with an input bitmap)
+// that fit on one SM for this shape.
+int scan_max_ctas_per_sm(int block_bits, int block, size_t smem, bool sparse);
 cudaError_t scan_set_smem_limit(int block_bits, size_t smem);
 
 }  // namespace pt

@@ -288,7 +288,10 @@ __device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord)
 
 // One CTA of a visit's scan: `cta` is its index in the visit's grid of
 // total_warps / (blockDim.x / 32) CTAs.  Every thread of the block calls it.
-template <int B, int KT>
+// DENSE = false leaves out the dense sub-round path (visits whose input is a
+// bitmap rarely have 32 full words in a row), which frees registers for a
+// third CTA per SM.
+template <int B, int KT, bool DENSE>
 __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f, int64_t cta, uint32_t crank,
                                          uint32_t* smem, ScanShared& sh) {
     ProbeEdge* s_pe = sh.pe;
@@ -511,7 +514,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     // before the current 8 are hashed, and the first 8 of the next dense
     // sub-round before the current one's last 8, so a warp keeps its key
     // loads in flight.
-    const bool dense_ok = n_in > 0 && s_pe[0].ncols == 1;
+    const bool dense_ok = DENSE && n_in > 0 && s_pe[0].ncols == 1;
     const ColRef d_col = s_pe[0].col[0];
     auto load8 = [&](uint32_t row0, uint64_t* kv) {
         if (d_col.dtype == 0) {
@@ -753,7 +756,17 @@ template <int B, int KT>
 __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ScanShared sh;
-    scan_cta<B, KT>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
+    scan_cta<B, KT, true>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
+}
+
+// The scan of a visit with an input bitmap (selection, backward pass, or the
+// survivors of a first-probe pass): no dense path, three CTAs per SM.
+template <int B, int KT>
+__global__ void __launch_bounds__(kScanMaxThreads, kScanSparseMinBlocks)
+    pt_scan_sparse_kernel(const VisitArgs a, const FilterCfg f) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ ScanShared sh;
+    scan_cta<B, KT, false>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
 }
 
 // Copy a visit's arguments from global memory into shared memory (all threads).
@@ -789,7 +802,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
         const BatchTask task = tasks[t];
         load_visit(s_a, visits + task.visit);
         __syncthreads();
-        scan_cta<B, KT>(s_a, f, (int64_t)task.part * C + rank, rank, smem, sh);
+        scan_cta<B, KT, true>(s_a, f, (int64_t)task.part * C + rank, rank, smem, sh);
         __syncthreads();
     }
 }
@@ -1120,6 +1133,14 @@ cudaError_t launch_maybe_cluster(K kernel, int cluster, int grid, int block, siz
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s) {
     const int c = a.cluster;
+    if (a.in_bits) {
+        if (f.block_bits == 512) {
+            if (f.k == 4) return launch_maybe_cluster(pt_scan_sparse_kernel<512, 4>, c, grid, block, smem, s, a, f);
+            return launch_maybe_cluster(pt_scan_sparse_kernel<512, 0>, c, grid, block, smem, s, a, f);
+        }
+        if (f.k == 4) return launch_maybe_cluster(pt_scan_sparse_kernel<256, 4>, c, grid, block, smem, s, a, f);
+        return launch_maybe_cluster(pt_scan_sparse_kernel<256, 0>, c, grid, block, smem, s, a, f);
+    }
     if (f.block_bits == 512) {
         if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<512, 4>, c, grid, block, smem, s, a, f);
         return launch_maybe_cluster(pt_scan_kernel<512, 0>, c, grid, block, smem, s, a, f);
@@ -1168,9 +1189,19 @@ cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int 
     return cudaGetLastError();
 }
 
-int scan_max_ctas_per_sm(int block_bits, int block, size_t smem) {
+int scan_max_ctas_per_sm(int block_bits, int block, size_t smem, bool sparse) {
     int n = 0, m = 0;
-    // every instantiation has the same launch bounds; take the smallest fit
+    // every instantiation of a kernel has the same launch bounds; take the smallest fit
+    if (sparse) {
+        if (block_bits == 512) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_sparse_kernel<512, 4>, block, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_sparse_kernel<512, 0>, block, smem);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_sparse_kernel<256, 4>, block, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_sparse_kernel<256, 0>, block, smem);
+        }
+        return n < m ? n : m;
+    }
     if (block_bits == 512) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_scan_kernel<512, 4>, block, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_scan_kernel<512, 0>, block, smem);
@@ -1186,9 +1217,13 @@ cudaError_t scan_set_smem_limit(int block_bits, size_t smem) {
     cudaError_t e;
     if (block_bits == 512) {
         if ((e = cudaFuncSetAttribute(pt_scan_kernel<512, 4>, at, (int)smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(pt_scan_sparse_kernel<512, 4>, at, (int)smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(pt_scan_sparse_kernel<512, 0>, at, (int)smem)) != cudaSuccess) return e;
         return cudaFuncSetAttribute(pt_scan_kernel<512, 0>, at, (int)smem);
     }
     if ((e = cudaFuncSetAttribute(pt_scan_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pt_scan_sparse_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pt_scan_sparse_kernel<256, 0>, at, (int)smem)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(pt_scan_kernel<256, 0>, at, (int)smem);
 }
 

@@ -100,6 +100,7 @@ struct pt_ctx {
     int scan_threads = 256;
     int smem_budget = 40 * 1024;  // more shared memory means less L1 for the filters probed through it
     int max_cluster = 1;  // 1: no clusters (remote probes measured slower than L2 ones)
+    int streams = 3;      // visits of a level spread over this many streams (1: one after another)
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
     bool shapes_ready = false;
@@ -292,13 +293,17 @@ constexpr int64_t kScanCtaSmem = 112 * 1024;
 constexpr int64_t kFirstCtaSmem = 46 * 1024;
 constexpr int kMaxCluster = 4;
 
-ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
+// sparse: the visit's scan reads an input bitmap (the scan kernel without the
+// dense path, which fits more CTAs per SM)
+ScanShape scan_shape(pt_ctx* ctx, const Visit& vis, bool sparse) {
     ScanShape s{};
     const int64_t n = ctx->tables[vis.table].n;
     const int64_t n_words = (n + 31) / 32;
     s.block = ctx->scan_threads;
     const int warps_per_cta = s.block / 32;
-    const size_t queues = (size_t)warps_per_cta * pt::scan_warp_smem_bytes((int)vis.in_edges.size());
+    // after a first-probe pass the scan probes one edge fewer
+    const int n_in = (int)vis.in_edges.size() - (vis.first && ctx->first_probe && sparse ? 1 : 0);
+    const size_t queues = (size_t)warps_per_cta * pt::scan_warp_smem_bytes(n_in);
     int64_t budget = std::min<int64_t>(ctx->smem_budget, kScanCtaSmem - (int64_t)queues);
     budget = std::max<int64_t>(0, budget) / 16 * 16;
     const int64_t want_filt = vis.in_edges.empty() ? 0 : std::min<int64_t>(budget, vis.max_in_filter_bytes);
@@ -307,7 +312,7 @@ ScanShape scan_shape(pt_ctx* ctx, const Visit& vis) {
     s.filter_smem = filt;
     // a cluster when some incoming filter may not fit one CTA's budget
     if (ctx->max_cluster > 1 && filt > 0 && vis.max_single_filter_bytes > (int64_t)filt) s.cluster = ctx->max_cluster;
-    int fit = pt::scan_max_ctas_per_sm(ctx->fcfg.block_bits, s.block, s.smem);
+    int fit = pt::scan_max_ctas_per_sm(ctx->fcfg.block_bits, s.block, s.smem, sparse);
     if (fit < 1) fit = 1;
     if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
     int64_t max_grid = (int64_t)ctx->num_sms * fit;
@@ -396,7 +401,10 @@ pt_status prepare_shapes(pt_ctx* ctx) {
         ctx->smem_attr_set[bi] = (int)kScanCtaSmem;
     }
     for (int p = 0; p < 2; ++p)
-        for (Visit& vis : ctx->visits[p]) vis.shape = scan_shape(ctx, vis);
+        for (Visit& vis : ctx->visits[p]) {
+            const bool sparse = p == 1 || ctx->tables[vis.table].sel != nullptr || (vis.first && ctx->first_probe);
+            vis.shape = scan_shape(ctx, vis, sparse);
+        }
     for (Visit& vis : ctx->visits[0]) {
         if (!vis.first) continue;
         // the filter budget of one CTA: the largest incoming filter, at most
@@ -414,7 +422,9 @@ pt_status prepare_shapes(pt_ctx* ctx) {
     return PT_OK;
 }
 
-pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st) {
+// kind: 0 scan, 1 size/clear + insert, 2 first probe; the pass and table of
+// the launch are kept beside it (kind | pass << 4 | table << 8).
+pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st, int pass, int table) {
     if (!ctx->timing) return PT_OK;
     std::vector<cudaEvent_t>& ev = ctx->capturing ? ctx->gev : ctx->ev;
     std::vector<int>& kinds = ctx->capturing ? ctx->gev_kind : ctx->ev_kind;
@@ -425,7 +435,7 @@ pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st) {
         ev.push_back(e);
         kinds.push_back(0);
     }
-    kinds[used] = kind;
+    kinds[used] = kind | (pass << 4) | (table << 8);
     if (ctx->capturing)  // becomes an event-record node of the graph, recorded at every replay
         PT_CUDA(ctx, cudaEventRecordWithFlags(ev[used], st, cudaEventRecordExternal));
     else
@@ -440,7 +450,7 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
     PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
     for (const Visit& vis : ctx->visits[p]) {
         const int v = vis.table;
-        cudaStream_t st = ctx->aux[ctx->slot[p][v] % pt_ctx::kAux];
+        cudaStream_t st = ctx->aux[ctx->slot[p][v] % ctx->streams];
         PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
         for (int e : vis.in_edges) {
             const int b = p == 0 ? ctx->src[e] : ctx->dst[e];  // the table that built the filter
@@ -453,39 +463,39 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         if (p == 0 && vis.first && ctx->first_probe) {
             // the first probe tests a filter of one of the lowest-level builders:
             // it waits for those only, on its own stream
-            cudaStream_t fs = ctx->fstream[v];
+            cudaStream_t fs = ctx->streams > 1 ? ctx->fstream[v] : st;
             PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
             int32_t lmin = INT32_MAX;
             for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->src[e]]);
             for (int e : vis.in_edges)
                 if (ctx->lvl[p][ctx->src[e]] == lmin) PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->src[e]], 0));
-            if ((s1 = record_event(ctx, 2, fs)) != PT_OK) return s1;
+            if ((s1 = record_event(ctx, 2, fs, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_probe_first(a, ctx->fcfg, ctx->mid[v], ctx->first_idx + v,
                                                 (int32_t)(vis.first_smem / 4), vis.first_grid, pt::kFirstThreads,
                                                 vis.first_smem, fs));
-            if ((s1 = record_event(ctx, 2, fs)) != PT_OK) return s1;
+            if ((s1 = record_event(ctx, 2, fs, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, cudaEventRecord(ctx->fev[v], fs));
             PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fev[v], 0));
             ctx->launches++;
             a.in_bits = ctx->mid[v];
             a.first_in = ctx->first_idx + v;
         }
-        if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
+        if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
         PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st));
-        if ((s1 = record_event(ctx, 0, st)) != PT_OK) return s1;
+        if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
         ctx->launches++;
         if (a.n_out > 0) {
             int64_t words = 0;
             for (int e : vis.out_edges) words = std::max(words, ctx->filt_max_words[e]);
             const int64_t n16 = words / 4;
             int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
-            if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
+            if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
             // up to three 512-thread CTAs per SM; segments are split between warps when
             // there are more warps than segments
             const int grid_i = std::max(1, std::min(3 * sh.total_warps / 16 + 1, ctx->num_sms * 3));
             PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, st));
-            if ((s1 = record_event(ctx, 1, st)) != PT_OK) return s1;
+            if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
             ctx->launches += 2;
         }
         PT_CUDA(ctx, cudaEventRecord(ctx->vev[p][v], st));
@@ -937,12 +947,26 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     return PT_OK;
 }
 
+pt_status pt_set_streams(pt_ctx* ctx, int32_t streams) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (streams < 1 || streams > pt_ctx::kAux) return fail(ctx, PT_ERR_INVALID, "streams must be 1..%d (got %d)", pt_ctx::kAux, streams);
+    if (streams != ctx->streams && ctx->gexec) {  // the captured launch sequence changes
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->streams = streams;
+    return PT_OK;
+}
+
 pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable) {
     if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
     if (enable != 0 && enable != 1) return fail(ctx, PT_ERR_INVALID, "enable must be 0 or 1 (got %d)", enable);
-    if (ctx->first_probe != (enable == 1) && ctx->gexec) {  // the captured launch sequence changes
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = nullptr;
+    if (ctx->first_probe != (enable == 1)) {  // the launch sequence and scan shapes change
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        ctx->shapes_ready = false;
     }
     ctx->first_probe = enable == 1;
     return PT_OK;
@@ -994,8 +1018,8 @@ pt_status kernel_times(pt_ctx* ctx, double* t, int* n) {
         for (size_t i = 0; i + 1 < used; i += 2) {
             float ms = 0.f;
             PT_CUDA(ctx, cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-            t[kinds[i]] += ms;
-            n[kinds[i]] += 1;
+            t[kinds[i] & 15] += ms;
+            n[kinds[i] & 15] += 1;
         }
         return PT_OK;
     };
@@ -1020,6 +1044,31 @@ pt_status pt_get_kernel_time(pt_ctx* ctx, double* scan_ms, int32_t* scan_launche
     if (scan_launches) *scan_launches = n[0] + n[2];
     if (other_ms) *other_ms = t[1];
     if (other_launches) *other_launches = n[1];
+    return PT_OK;
+}
+
+pt_status pt_get_launch_times(pt_ctx* ctx, int32_t max, pt_launch_time* out, int32_t* n_out) {
+    if (!ctx || !n_out || (max > 0 && !out)) return fail(ctx, PT_ERR_INVALID, "ctx, out or n_out is NULL");
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const bool graph = ctx->gexec && ctx->graph_timed && ctx->graph_replays > 0;
+    const std::vector<cudaEvent_t>& ev = graph ? ctx->gev : ctx->ev;
+    const std::vector<int>& kinds = graph ? ctx->gev_kind : ctx->ev_kind;
+    const size_t used = graph ? ctx->gev_used : ctx->ev_used;
+    int32_t n = 0;
+    for (size_t i = 0; i + 1 < used; i += 2, ++n) {
+        if (n >= max) continue;
+        float ms = 0.f, start = 0.f;
+        PT_CUDA(ctx, cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+        PT_CUDA(ctx, cudaEventElapsedTime(&start, ev[0], ev[i]));
+        pt_launch_time& o = out[n];
+        std::memset(&o, 0, sizeof o);
+        o.kind = kinds[i] & 15;
+        o.pass = (kinds[i] >> 4) & 15;
+        o.table = kinds[i] >> 8;
+        o.start_ms = start;
+        o.ms = ms;
+    }
+    *n_out = n;
     return PT_OK;
 }
 

@@ -139,7 +139,7 @@ extern "C" pt_status pt_visit_static(const pt_filter_cfg* cfg, void* cuda_stream
     const size_t queues = (size_t)warps_per_cta * pt::scan_warp_smem_bytes(n_in);
     const size_t filt = n_in > 0 ? (46 * 1024 - queues) / 16 * 16 : 0;
     const size_t smem = filt + queues;
-    int fit = pt::scan_max_ctas_per_sm(cfg->block_bits, block, smem);
+    int fit = pt::scan_max_ctas_per_sm(cfg->block_bits, block, smem, in_bits != nullptr);
     if (fit < 1) fit = 1;
     const int64_t n_words = (n_rows + 31) / 32;
     int64_t grid = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;

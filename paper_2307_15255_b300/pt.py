@@ -51,6 +51,11 @@ class pt_visit_stats(C.Structure):
                 ("first_probe_sectors", C.c_int64)]
 
 
+class pt_launch_time(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pass_", C.c_int32), ("table", C.c_int32), ("reserved", C.c_int32),
+                ("start_ms", C.c_double), ("ms", C.c_double)]
+
+
 class pt_kernel_times(C.Structure):
     _fields_ = [("first_ms", C.c_double), ("scan_ms", C.c_double), ("build_ms", C.c_double),
                 ("first_launches", C.c_int32), ("scan_launches", C.c_int32), ("build_pairs", C.c_int32),
@@ -97,7 +102,9 @@ _SIGS = {
     "pt_set_kernel_timing": (C.c_int, [_P, C.c_int32]),
     "pt_set_cluster": (C.c_int, [_P, C.c_int32]),
     "pt_set_first_probe": (C.c_int, [_P, C.c_int32]),
+    "pt_set_streams": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
+    "pt_get_launch_times": (C.c_int, [_P, C.c_int32, C.POINTER(pt_launch_time), C.POINTER(C.c_int32)]),
     "pt_get_kernel_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "pt_get_launch_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
@@ -267,6 +274,20 @@ def pt_get_kernel_times(ctx: int) -> dict:
     t = pt_kernel_times()
     _check(lib.pt_get_kernel_times(ctx, C.byref(t)), "pt_get_kernel_times", ctx)
     return {f: getattr(t, f) for f, _ in pt_kernel_times._fields_ if f != "reserved"}
+
+
+def pt_get_launch_times(ctx: int) -> list:
+    n = C.c_int32()
+    _check(lib.pt_get_launch_times(ctx, 0, None, C.byref(n)), "pt_get_launch_times", ctx)
+    arr = (pt_launch_time * max(n.value, 1))()
+    _check(lib.pt_get_launch_times(ctx, n.value, arr, C.byref(n)), "pt_get_launch_times", ctx)
+    kinds = {0: "scan", 1: "build", 2: "first"}
+    return [{"kind": kinds[t.kind], "pass": t.pass_, "table": t.table, "start_ms": t.start_ms, "ms": t.ms}
+            for t in arr[:n.value]]
+
+
+def pt_set_streams(ctx: int, streams: int) -> None:
+    _check(lib.pt_set_streams(ctx, streams), "pt_set_streams", ctx)
 
 
 def pt_set_first_probe(ctx: int, enable: bool) -> None:

@@ -121,10 +121,12 @@ def test_graph_mode_host_columns_and_repeat(oracle_lib):
     from _gpu import assert_same, collect, session_for
     w = W.snowflake(scale=0.02, int64=True, composite=True, bits_per_key=10)
     want = oracle_lib.transfer(w)
+    import paper_2307_15255_b300.pt as P
     for kw in ({"graph": True}, {"host": True, "pin": True}, {"host": True}):
         s = session_for(w, **kw)
         try:
-            for _ in range(3):  # replays and reruns give the same bits
+            for i in range(3):  # replays and reruns give the same bits, on 3 streams or 1
+                P.pt_set_streams(s.ctx, 1 if i == 1 else 3)
                 s.run()
                 assert_same(collect(s, w), want, w)
         finally:
@@ -218,6 +220,12 @@ def test_kernel_timing_direct_and_graph():
         kt = P.pt_get_kernel_time(s.ctx)  # the last replay
         assert kt["scan_launches"] == 2 * w.n_tables and kt["scan_ms"] > 0
         assert P.pt_get_launch_count(s.ctx) - n0 == 3 * (P.pt_get_launch_count(s.ctx) - n0) // 3 > 0
+        # the same events one launch at a time: one scan per (pass, table), times adding up
+        lt = P.pt_get_launch_times(s.ctx)
+        scans = [(x["pass"], x["table"]) for x in lt if x["kind"] == "scan"]
+        assert sorted(scans) == sorted((p, v) for p in range(2) for v in range(w.n_tables))
+        assert abs(sum(x["ms"] for x in lt if x["kind"] == "scan") - kt["scan_ms"]) < 1e-3
+        assert all(x["ms"] > 0 and x["start_ms"] >= 0 for x in lt)
     finally:
         s.close()
 
