@@ -877,15 +877,20 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
             probe_global_n<B, KT, R>(fg, nb, h, k, pass);
     };
     // the tile's survivor words: word i is ballot i; lanes 0..7 store one each
+    // (every lane holds all 8 ballots; lane 0 stores them as two 16-byte
+    // writes: the tile's words start 32-byte aligned, and the bitmap's
+    // allocation covers whole tiles, so the last tile's words past the table
+    // land in its padding, which no reader looks at)
+    static_assert(R == 8, "a tile is 8 bitmap words");
     auto store = [&](int64_t t, const bool* pass) {
-        uint32_t myw = 0;
+        uint32_t m[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const uint32_t m = __ballot_sync(FULL, pass[i]);
-            if (lane == (uint32_t)i) myw = m;
+        for (int i = 0; i < R; ++i) m[i] = __ballot_sync(FULL, pass[i]);
+        if (lane == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(mid + t * R);
+            dst[0] = make_uint4(m[0], m[1], m[2], m[3]);
+            dst[1] = make_uint4(m[4], m[5], m[6], m[7]);
         }
-        const int64_t w = t * R + lane;
-        if (lane < (uint32_t)R && w < n_words) mid[w] = myw;
     };
 
     if (ncols == 1 && c0.dtype != 0) {
@@ -910,8 +915,13 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
             for (int i = 0; i < R; ++i) h[i] = kv[i];
             if (t + W < n_tiles) load(t + W, kv);
             if (!hashed) {
+                if (seed == 0) {  // x ^ 0 = x: two integer-ALU operations per key fewer
 #pragma unroll
-                for (int i = 0; i < R; ++i) h[i] = hash_key(h[i], seed);
+                    for (int i = 0; i < R; ++i) h[i] = mix64(h[i] + kGamma);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) h[i] = hash_key(h[i], seed);
+                }
             }
             bool pass[R];
             probe(h, pass);

@@ -289,9 +289,8 @@ pt_status check_columns(pt_ctx* ctx, int64_t n_rows, int32_t n_cols, const pt_co
 constexpr int64_t kScanCtaSmem = 112 * 1024;
 // Dynamic shared memory of a first-probe CTA: below the default 48 KB limit
 // (which also covers the kernel's static shared memory), so no kernel
-// attribute is needed; four such CTAs leave most of an SM's 228 KB to L1.
+// attribute is needed.
 constexpr int64_t kFirstCtaSmem = 46 * 1024;
-constexpr int kMaxCluster = 4;
 
 // sparse: the visit's scan reads an input bitmap (the scan kernel without the
 // dense path, which fits more CTAs per SM)
@@ -448,7 +447,15 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
     if (!ctx->shapes_ready) return fail(ctx, PT_ERR_STATE, "launch shapes not prepared");
     PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
     PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
-    for (const Visit& vis : ctx->visits[p]) {
+    // enqueue by level (then visiting order): a stream never holds a visit
+    // behind one of a higher level, which would delay it for nothing
+    std::vector<const Visit*> seq;
+    for (const Visit& vis : ctx->visits[p]) seq.push_back(&vis);
+    std::stable_sort(seq.begin(), seq.end(), [&](const Visit* x, const Visit* y) {
+        return ctx->lvl[p][x->table] < ctx->lvl[p][y->table];
+    });
+    for (const Visit* vp : seq) {
+        const Visit& vis = *vp;
         const int v = vis.table;
         cudaStream_t st = ctx->aux[ctx->slot[p][v] % ctx->streams];
         PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
@@ -744,8 +751,8 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         if (has_edge[v]) off += align_up(std::max<size_t>((size_t)n[v] * 4, 16));
         o_seg[v] = off;
         if (has_edge[v]) off += align_up((size_t)ctx->seg_cap * 4);
-        o_mid[v] = off;
-        if (has_mid[v]) off += align_up(std::max<size_t>(wb, 16));
+        o_mid[v] = off;  // whole 256-row tiles: the first-probe kernel writes 8 words at a time
+        if (has_mid[v]) off += align_up((size_t)((n[v] + 255) / 256) * 32);
     }
     for (int e = 0; e < E; ++e)
         for (int p = 0; p < 2; ++p) {
