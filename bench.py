@@ -61,7 +61,9 @@ def workload_desc(w) -> dict:
         "edges": len(w.edges),
         "bits_per_key": w.bits_per_key, "k": w.k, "block_bits": w.block_bits,
         "passes": "forward+backward",
-        "l2": f"inputs larger than L2 (working set {w.nbytes() / 1e9:.2f} GB vs 126 MB), no flush",
+        "l2": (f"inputs larger than L2 (working set {w.nbytes() / 1e9:.2f} GB vs 126 MB), no flush"
+               if w.nbytes() > 126e6 else
+               f"working set {w.nbytes() / 1e9:.3f} GB fits the 126 MB L2 (no flush: a small-scale run)"),
     }
 
 
