@@ -88,3 +88,17 @@ def test_plan_graph_random_graphs(P, oracle_lib):
         got = P.pt_plan_graph(n, [(e.t0, e.c0, e.t1, e.c1) for e in edges])
         want = oracle_lib.orient(n, edges)
         assert got["src"] == want["src"] and got["dst"] == want["dst"] and got["order"] == want["order"]
+
+
+def test_context_calls_reject_a_null_context(P):
+    # every per-context setter and getter answers PT_ERR_INVALID for ctx = NULL
+    # on the host, before touching a device
+    n = ctypes.c_int32()
+    kt = P.pt_kernel_times()
+    for name, args in (("pt_set_streams", (None, 1)), ("pt_set_first_probe", (None, 1)),
+                       ("pt_set_cluster", (None, 1)), ("pt_set_kernel_timing", (None, 1)),
+                       ("pt_set_graph_mode", (None, 1)), ("pt_set_launch", (None, 256, 0, 0)),
+                       ("pt_get_kernel_times", (None, ctypes.byref(kt))),
+                       ("pt_get_launch_times", (None, 0, None, ctypes.byref(n))),
+                       ("pt_run_transfer", (None,)), ("pt_plan", (None, None, None))):
+        assert getattr(P.lib, name)(*args) == P.PT_ERR_INVALID, name
