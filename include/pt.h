@@ -346,11 +346,10 @@ pt_status pt_server_destroy(pt_server* srv);
 
 /* ---- one visit without any allocation ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: code running while a stream is being
- * captured into a CUDA graph (allocation calls are not allowed there),
- * engines that give all device memory to their own pool up front, and
- * services that must not meet an out-of-memory error in the middle of a
- * query.  pt_visit_static runs one filter transformation (Section 3.2, Fig.
+ * that cannot allocate device memory: engines that give all device memory
+ * to their own pool up front, paths where an allocation (which can
+ * synchronize the device) is not acceptable, and services that must not
+ * meet an out-of-memory error in the middle of a query.  pt_visit_static runs one filter transformation (Section 3.2, Fig.
  * 2) -- probe, survivor bitmap, compaction, size/clear and insert -- with
  * every input and output supplied by the caller.  Its scratch (compacted
  * row ids, per-warp segment lengths, counters) is a fixed array of about

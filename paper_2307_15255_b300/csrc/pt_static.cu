@@ -1,9 +1,10 @@
 // pt_visit_static: one transfer visit that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph
-// capture (where allocation calls are not allowed), engines that hand all
-// device memory to their own pool up front and forbid other allocations,
-// and hosts that must not fail with an out-of-memory error mid-query.  For
+// Some callers cannot call cudaMalloc: engines that hand all device memory
+// to their own pool up front and forbid other allocations, latency-bound
+// paths where an allocation (which can synchronize the device) is not
+// acceptable, and hosts that must not fail with an out-of-memory error
+// mid-query.  For
 // them this entry point runs the same three kernels as a planned context
 // (scan, size/clear, insert) for a single visit, with every input and
 // output supplied by the caller and the kernels' scratch -- the compacted
@@ -133,11 +134,15 @@ extern "C" pt_status pt_visit_static(const pt_filter_cfg* cfg, void* cuda_stream
 
     // Launch shape within the default 48 KB of shared memory per CTA (46 KB
     // dynamic plus the kernel's static part), so no kernel attribute is
-    // changed: 256 threads (128 with many incoming edges).
-    const int block = n_in > 4 ? 128 : 256;
-    const int warps_per_cta = block / 32;
+    // changed: the most warps (8, 4, 2 or 1) whose per-warp queues fit, and
+    // the rest of the 46 KB for filters.
+    constexpr size_t kStaticSmem = 46 * 1024;
+    int warps_per_cta = 8;
+    while (warps_per_cta > 1 && (size_t)warps_per_cta * pt::scan_warp_smem_bytes(n_in) > kStaticSmem) warps_per_cta /= 2;
+    const int block = warps_per_cta * 32;
     const size_t queues = (size_t)warps_per_cta * pt::scan_warp_smem_bytes(n_in);
-    const size_t filt = n_in > 0 ? (46 * 1024 - queues) / 16 * 16 : 0;
+    if (queues > kStaticSmem) return fail(PT_ERR_UNSUPPORTED, "%d incoming filters need more shared memory than 46 KB", n_in);
+    const size_t filt = n_in > 0 ? (kStaticSmem - queues) / 16 * 16 : 0;
     const size_t smem = filt + queues;
     int fit = pt::scan_max_ctas_per_sm(cfg->block_bits, block, smem, in_bits != nullptr);
     if (fit < 1) fit = 1;

@@ -1,9 +1,9 @@
 """The allocation-free entry point pt_visit_static against the planned path.
 
-pt_visit_static serves callers that cannot allocate device memory (code
-that runs during CUDA graph capture, engines that own all device memory
-through their own pool, services that must not hit out-of-memory mid
-query).  It runs one visit with caller-owned inputs and outputs and keeps
+pt_visit_static serves callers that cannot allocate device memory
+(engines that own all device memory through their own pool, services that
+must not hit out-of-memory mid query, paths where an allocation's implicit
+device synchronization is not acceptable).  It runs one visit with caller-owned inputs and outputs and keeps
 its scratch in a fixed device array.  Here it redoes single visits of a
 transfer that a planned context ran, from the same incoming filters, and
 must reproduce that context's survivor bitmap, survivor count, outgoing
@@ -102,6 +102,39 @@ def test_static_visits_match_planned_context(ran):
             want = s.filter(0, e).cpu().numpy().view(np.uint32)
             assert nb == len(want) * 32 // w.block_bits, e
             assert np.array_equal(words, want), e
+
+
+@pytest.mark.parametrize("n_dims", [5, 8])
+def test_static_visit_with_many_incoming_filters(n_dims):
+    # five and eight incoming filters need more queue space per warp, so the
+    # entry point runs fewer warps per CTA to stay within its shared memory;
+    # the survivors must not change, on two calls in a row
+    from _gpu import device_tables, edges_of
+    from paper_2307_15255_b300.session import TransferSession
+    rng = np.random.default_rng(40 + n_dims)
+    nv = 200_003
+    dims, cols, edges = [], [], []
+    for j in range(n_dims):
+        nd = 500 + 300 * j
+        d = rng.permutation(nd).astype(np.int64) * 3 - 7
+        dims.append(W.Table(f"D{j}", nd, [d], ["id"], W.bitmap_from_bools(rng.random(nd) < 0.8)))
+        cols.append(d[rng.integers(0, nd, nv)])
+        edges.append(W.Edge(0, (j,), j + 1, (0,)))
+    V = W.Table("V", nv, cols, [f"k{j}" for j in range(n_dims)], None)
+    w = W.Workload("many_filters", [V] + dims, edges, 16, 4, 256, 0)
+    tables = device_tables(w)
+    s = TransferSession(tables, edges_of(w), w.bits_per_key, w.k, w.block_bits, w.seed)
+    try:
+        s.run()
+        torch.cuda.synchronize()
+        bits, cnt = _planned(s, w, 0)
+        assert cnt > 0
+        for _ in range(2):
+            got = _visit(w, tables, s, 0)
+            assert np.array_equal(got["bits"], bits)
+            assert got["count"] == cnt
+    finally:
+        s.close()
 
 
 def test_static_visit_rejects_too_many_rows():
