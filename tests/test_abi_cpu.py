@@ -88,6 +88,17 @@ def test_plan_graph_random_graphs(P, oracle_lib):
         got = P.pt_plan_graph(n, [(e.t0, e.c0, e.t1, e.c1) for e in edges])
         want = oracle_lib.orient(n, edges)
         assert got["src"] == want["src"] and got["dst"] == want["dst"] and got["order"] == want["order"]
+        # level = longest path from a source of the oriented DAG, by brute force
+        # over paths (the probe order and the first-probe schedule use it)
+        for v in range(nt):
+            preds = [s_ for s_, d in zip(want["src"], want["dst"]) if d == v]
+
+            def depth(u):
+                ps = [s_ for s_, d in zip(want["src"], want["dst"]) if d == u]
+                return max([1 + depth(x) for x in ps], default=0)
+
+            assert got["level"][v] == depth(v), (s, v)
+            assert all(got["level"][v] > got["level"][u] for u in preds)
 
 
 def test_context_calls_reject_a_null_context(P):
