@@ -26,13 +26,17 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pt_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile pt_oracle.c into liboracle.so next to it (gcc, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", _LIB, _SRC]
-        subprocess.check_call(cmd)
+    """Compile pt_oracle.c into liboracle.so next to it (gcc, -O2), and the
+    same source with OpenMP into liboracle_omp.so (multi-core timing only)."""
+    for lib_path, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+            cmd = ["gcc", "-O2", "-std=c11", "-Wall", *extra, "-shared", "-fPIC", "-o", lib_path + ".tmp", _SRC]
+            subprocess.check_call(cmd)
+            os.replace(lib_path + ".tmp", lib_path)
     return _LIB
 
 
@@ -52,36 +56,55 @@ class _Cfg(C.Structure):
 
 
 _lib = None
+_lib_omp = None
+
+
+def _declare(L):
+    L.o_hash1.restype = C.c_uint64
+    L.o_hash1.argtypes = [C.c_uint64, C.c_uint64]
+    L.o_hash2.restype = C.c_uint64
+    L.o_hash2.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+    L.o_key.restype = C.c_uint64
+    L.o_key.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+    L.o_nblocks.restype = C.c_int64
+    L.o_nblocks.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32]
+    L.o_block_of.restype = C.c_int64
+    L.o_block_of.argtypes = [C.c_uint64, C.c_int64]
+    L.o_bits_of.restype = None
+    L.o_bits_of.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+    L.o_filter_insert.restype = None
+    L.o_filter_insert.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64]
+    L.o_filter_probe.restype = C.c_int
+    L.o_filter_probe.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64]
+    L.o_orient.restype = C.c_int
+    L.o_orient.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p]
+    L.o_transfer.restype = C.c_int
+    L.o_transfer.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p]
+    L.o_set_threads.restype = C.c_int
+    L.o_set_threads.argtypes = [C.c_int32]
+    return L
 
 
 def lib():
+    """The plain (single-threaded) oracle."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        _lib.o_hash1.restype = C.c_uint64
-        _lib.o_hash1.argtypes = [C.c_uint64, C.c_uint64]
-        _lib.o_hash2.restype = C.c_uint64
-        _lib.o_hash2.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
-        _lib.o_key.restype = C.c_uint64
-        _lib.o_key.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
-        _lib.o_nblocks.restype = C.c_int64
-        _lib.o_nblocks.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32]
-        _lib.o_block_of.restype = C.c_int64
-        _lib.o_block_of.argtypes = [C.c_uint64, C.c_int64]
-        _lib.o_bits_of.restype = None
-        _lib.o_bits_of.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
-        _lib.o_filter_insert.restype = None
-        _lib.o_filter_insert.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64]
-        _lib.o_filter_probe.restype = C.c_int
-        _lib.o_filter_probe.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_uint64]
-        _lib.o_orient.restype = C.c_int
-        _lib.o_orient.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
-                                  C.c_void_p, C.c_void_p]
-        _lib.o_transfer.restype = C.c_int
-        _lib.o_transfer.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
-                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                    C.c_void_p]
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def lib_threads(threads: int):
+    """The OpenMP build of the same source, set to ``threads`` threads.
+    Returns the library and the thread count it will use."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _declare(C.CDLL(_LIB_OMP))
+    used = int(_lib_omp.o_set_threads(int(threads)))
+    return _lib_omp, used
 
 
 # ---- single-function views -------------------------------------------------
@@ -161,15 +184,16 @@ def max_filter_words(n0: int, n1: int, bits_per_key: int, block_bits: int) -> in
 
 # ---- the whole transfer ----------------------------------------------------
 
-def transfer(w, exact: bool = False, seed: Optional[int] = None) -> Dict[str, list]:
+def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 1) -> Dict[str, list]:
     """Forward + backward predicate transfer over workload ``w``.
 
     Returns ``surv[p][v]`` (uint32 bitmaps), ``count[p][v]``,
     ``filters[p][e]`` (uint32 words, Bloom mode), ``nblocks[p][e]`` and
     ``sectors[p][v] = (probe_sectors, build_sectors)``; ``p`` is 0 for the
-    forward pass and 1 for the backward pass.
+    forward pass and 1 for the backward pass.  ``threads`` > 1 runs the
+    OpenMP build of the same source (identical results; timing only).
     """
-    L = lib()
+    L = lib() if threads <= 1 else lib_threads(threads)[0]
     nt, ne = w.n_tables, len(w.edges)
     keep = []  # keep ctypes buffers alive during the call
     ta = (_Table * nt)()

@@ -43,10 +43,19 @@
  *           c_b / n_b (survivors of the building visit over its table's
  *           rows, the LIP-style ordering of Section 3.2), then edge id; the
  *           order never changes a result, only how many key sectors are read.
+ *
+ * Threads: built plainly (liboracle.so) every loop runs on one thread.  The
+ * same source built with -fopenmp (liboracle_omp.so, timing only) splits
+ * the per-row loops across threads; every row is still handled by the same
+ * statements, the survivor words are formed per word, and filter words are
+ * OR-ed atomically, so both builds give identical results.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int64_t n_rows;
@@ -112,7 +121,10 @@ void o_filter_insert(uint32_t* words, int64_t nblocks, int32_t block_bits, int32
     int32_t pos[64];
     int64_t base = o_block_of(h, nblocks) * (block_bits / 32);
     o_bits_of(h, block_bits, k, pos);
-    for (int32_t i = 0; i < k; i++) words[base + (pos[i] >> 5)] |= 1u << (pos[i] & 31);
+    for (int32_t i = 0; i < k; i++) {
+#pragma omp atomic update
+        words[base + (pos[i] >> 5)] |= 1u << (pos[i] & 31);
+    }
 }
 
 int o_filter_probe(const uint32_t* words, int64_t nblocks, int32_t block_bits, int32_t k, uint64_t h) {
@@ -122,6 +134,17 @@ int o_filter_probe(const uint32_t* words, int64_t nblocks, int32_t block_bits, i
     for (int32_t i = 0; i < k; i++)
         if (!((words[base + (pos[i] >> 5)] >> (pos[i] & 31)) & 1u)) return 0;
     return 1;
+}
+
+/* threads the per-row loops use (the OpenMP build; 1 in the plain build) */
+int o_set_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ---- predicate transfer graph and order (Section 3.2) ---------------- */
@@ -186,7 +209,8 @@ static int o_bit(const uint32_t* bm, int64_t r) { return (int)((bm[r >> 5] >> (r
  * whose flag is set (row r lives in sector (r * w) / 32)                 */
 static int64_t o_sectors(const unsigned char* flag, int64_t n, int32_t w) {
     int64_t per = 32 / w, cnt = 0;
-    for (int64_t s = 0; s * per < n; s++) {
+#pragma omp parallel for schedule(static) reduction(+ : cnt)
+    for (int64_t s = 0; s < (n + per - 1) / per; s++) {
         int any = 0;
         for (int64_t r = s * per; r < (s + 1) * per && r < n; r++) any |= flag[r];
         cnt += any;
@@ -246,6 +270,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
             unsigned char* alive = (unsigned char*)malloc((size_t)(n > 0 ? n : 1));
             int64_t c = 0, probe_sec = 0, build_sec = 0;
 
+#pragma omp parallel for schedule(static)
             for (int64_t r = 0; r < n; r++) alive[r] = in ? (unsigned char)o_bit(in, r) : 1;
 
             /* incoming edges of v in this pass; v's level is one more than
@@ -283,6 +308,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
                 o_side(ed, v, &cs);
                 for (j = 0; j < ed->ncols; j++)
                     probe_sec += o_sectors(alive, n, t[v].dtypes[cs[j]] == 0 ? 4 : 8);
+#pragma omp parallel for schedule(static)
                 for (int64_t r = 0; r < n; r++) {
                     if (!alive[r]) continue;
                     if (exact) {
@@ -298,10 +324,14 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
                 }
             }
 
-            /* survivor bitmap, tail bits zero */
-            for (int64_t w = 0; w < (n + 31) / 32; w++) out[w] = 0;
-            for (int64_t r = 0; r < n; r++)
-                if (alive[r]) { out[r >> 5] |= 1u << (r & 31); c++; }
+            /* survivor bitmap, one word per 32 rows, tail bits zero */
+#pragma omp parallel for schedule(static) reduction(+ : c)
+            for (int64_t w = 0; w < (n + 31) / 32; w++) {
+                uint32_t x = 0;
+                for (int64_t r = 32 * w; r < 32 * w + 32 && r < n; r++)
+                    if (alive[r]) { x |= 1u << (r & 31); c++; }
+                out[w] = x;
+            }
             count[p * n_tables + v] = c;
 
             /* build one fresh outgoing filter per outgoing edge from the survivors' keys */
@@ -335,6 +365,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
                     int64_t nb = o_nblocks(c, n_rows[other], cfg->bits_per_key, B);
                     uint32_t* f = filt[p * n_edges + i];
                     memset(f, 0, sizeof(uint32_t) * (size_t)(nb * wpb));
+#pragma omp parallel for schedule(static)
                     for (int64_t r = 0; r < n; r++)
                         if (alive[r]) o_filter_insert(f, nb, B, K, o_edge_hash(&t[v], ed, v, r, cfg->seed));
                     nblocks[p * n_edges + i] = nb;

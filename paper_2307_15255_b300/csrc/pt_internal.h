@@ -22,6 +22,9 @@ constexpr int kFirstThreads = 256;    // first-probe CTA size (launch bounds)
 constexpr int kFirstMinBlocks = 3;    // first-probe CTAs per SM the register budget allows
 constexpr int kFirstTileRows = 256;   // rows a first-probe warp takes at a time (8 bitmap words)
 constexpr int64_t kFirstMinRows = 1 << 20;  // smaller visits keep their first probe in the scan kernel
+constexpr int kListThreads = 256;     // backward list-probe CTA size (launch bounds)
+constexpr int kListMinBlocks = 3;     // its CTAs per SM the register budget allows
+constexpr int kListRows = 4;          // listed survivors per lane of a batch
 
 // Word offset of stage s's queue inside a warp's queue area, and the area's size.
 __host__ __device__ inline int qoff(int s) { return s * kQueueCap; }
@@ -58,6 +61,8 @@ struct ProbeEdge {
     int64_t build_rows;                       // rows of the building table
     int32_t build_level;                      // the building visit's level in this pass's DAG
     int32_t pad;
+    const uint64_t* hin;                      // backward list probe: this edge's key hash of every
+                                              // listed survivor (slot-aligned with list_ids), or nullptr
 };
 
 // An outgoing edge: the visit's key column(s) and the filter it builds.
@@ -68,6 +73,8 @@ struct BuildEdge {
     uint32_t* filter;
     int64_t* nblocks;
     int64_t probe_rows;  // rows of the table at the other end (size rule)
+    uint64_t* hout;      // the insert also stores each survivor's key hash here (slot-aligned with
+                         // ids), for the backward pass's probe of this edge; nullptr: not stored
 };
 
 struct FilterCfg {
@@ -84,7 +91,7 @@ struct VisitArgs {
     int64_t n;                       // rows
     const uint32_t* in_bits;         // input bitmap or nullptr (= all rows)
     uint32_t* out_bits;              // survivor bitmap
-    uint32_t* ids;                   // compacted survivor row ids (nullptr: visit builds nothing)
+    uint32_t* ids;                   // compacted survivor row ids (nullptr: not needed by any later step)
     uint32_t* seg_count;             // survivors per scan warp (segment), nullptr if ids is
     unsigned long long* count;       // total survivors (zeroed before the pass)
     unsigned long long* stats;       // [0] probe sectors, [1] build sectors (zeroed before the pass);
@@ -99,6 +106,9 @@ struct VisitArgs {
     int32_t pad_;
     const int32_t* first_in;         // in[] index of the edge a first-probe pass already tested
                                      // (in_bits then holds its survivors), or nullptr
+    const uint32_t* list_ids;        // backward list probe: the forward survivors' ids, in segments
+                                     // of words_per_warp * 32 slots (total_warps segments)
+    const uint32_t* list_seg;        // survivors per forward segment
     ProbeEdge in[kMaxIn];
     BuildEdge out[kMaxOut];
     ColRef bcol[kMaxBuildCols];
@@ -127,6 +137,13 @@ cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int bl
                         cudaStream_t s);
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
 cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+// launch_probe_list: a backward visit over the forward survivors listed at
+// a.list_ids / a.list_seg, probing with the stored hashes in[].hin; writes
+// a.out_bits (every word of the table), a.ids / a.seg_count (same segment
+// geometry), a.count and a.stats.  grid * block / 32 warps walk the
+// a.total_warps segments.
+cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s);
+cudaError_t probe_list_set_smem_limit(int block_bits, size_t smem);
 
 // Batched launches read their task range {first, count} from device memory
 // (range[0], range[1]) so that one captured graph serves every batch.

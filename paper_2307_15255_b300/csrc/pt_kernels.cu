@@ -93,6 +93,22 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
     return v;
 }
 
+// Block-wide copy of n16 16-byte chunks from global into shared memory, with
+// four independent loads per thread in flight (a filter copy then costs one
+// or two L2 round trips, not one per chunk a thread moves).
+__device__ __forceinline__ void copy_to_smem(uint4* dst, const uint4* __restrict__ src, uint32_t n16) {
+    constexpr uint32_t U = 4;
+    uint32_t t = threadIdx.x;
+    for (; t + (U - 1) * blockDim.x < n16; t += U * blockDim.x) {
+        uint4 v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) v[u] = __ldg(src + t + u * blockDim.x);
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) dst[t + u * blockDim.x] = v[u];
+    }
+    for (; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
+}
+
 // Address in CTA `rank` of this cluster of the shared-memory location at
 // (this CTA's) shared-window address `addr`, and a load through it.
 __device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
@@ -180,6 +196,40 @@ __device__ __forceinline__ void probe_global_n(const uint32_t* __restrict__ f, u
         bi[i] = mul_hi((uint32_t)(h[i] >> 32), nb);
         const uint32_t w0 = mul_hi(mad_lo(lo[i], BB::SCALE, 0u), BB::WPB);
         pass[i] = rot_r(__ldg(f + (size_t)bi[i] * BB::WPB + w0), lo[i]) & 1u;
+    }
+    const int kk = KT > 0 ? KT : k;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if (pass[i]) {
+            const uint32_t* blk = f + (size_t)bi[i] * BB::WPB;
+            const uint32_t h2 = (lo[i] >> 16) | 1u;
+            uint32_t ok = 0xFFFFFFFFu;
+#pragma unroll 4
+            for (int t = 1; t < kk; ++t) {
+                const uint32_t at = mad_lo((uint32_t)t, h2, lo[i]);
+                ok &= rot_r(__ldg(blk + mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB)), at);
+            }
+            pass[i] = ok & 1u;
+        }
+    }
+}
+
+// probe_global_n for rows of which only some are live: a row that is not
+// live issues no load and does not pass.
+template <int B, int KT, int R>
+__device__ __forceinline__ void probe_global_live(const uint32_t* __restrict__ f, uint32_t nb, const uint64_t* h,
+                                                  int k, const bool* live, bool* pass) {
+    using BB = BlockBits<B>;
+    uint32_t lo[R], bi[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        lo[i] = (uint32_t)h[i];
+        bi[i] = mul_hi((uint32_t)(h[i] >> 32), nb);
+        pass[i] = false;
+        if (live[i]) {
+            const uint32_t w0 = mul_hi(mad_lo(lo[i], BB::SCALE, 0u), BB::WPB);
+            pass[i] = rot_r(__ldg(f + (size_t)bi[i] * BB::WPB + w0), lo[i]) & 1u;
+        }
     }
     const int kk = KT > 0 ? KT : k;
 #pragma unroll
@@ -340,8 +390,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         const uint4* src = reinterpret_cast<const uint4*>(s_pe[i].filter);
         uint4* dst = reinterpret_cast<uint4*>(smem + s_off[i]);
         if (!s_split[i]) {
-            const uint32_t n16 = s_nb[i] * (WPB / 4);
-            for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
+            copy_to_smem(dst, src, s_nb[i] * (WPB / 4));
         } else {
             // this CTA's part: blocks crank, crank + C, crank + 2C, ...
             const uint32_t nl = (s_nb[i] + C - 1 - crank) >> lc;
@@ -851,7 +900,7 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
     if (in_smem) {
         const uint4* src = reinterpret_cast<const uint4*>(s_pe.filter);
         uint4* dst = reinterpret_cast<uint4*>(smem);
-        for (uint32_t t = threadIdx.x; t < nb * (WPB / 4); t += blockDim.x) dst[t] = __ldg(src + t);
+        copy_to_smem(dst, src, nb * (WPB / 4));
     }
     __syncthreads();
 
@@ -968,6 +1017,187 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
 }
 
 // ---------------------------------------------------------------------------
+// 1b. a backward visit over the forward pass's compacted survivors
+//
+// The backward pass reverses every edge and starts each table from what
+// survived its forward visit (Section 3.2, "Transfer Schedule").  So the
+// filters a table probes in the backward pass are on exactly the edges it
+// built in the forward pass, and the forward insert stored, beside each
+// survivor's row id, the hash of its key on each of those edges.  This
+// kernel therefore reads no key column and no input bitmap: warp w walks
+// forward segment s = w, w + W, ... -- row ids and hashes in coalesced 4-
+// and 8-byte loads, kListRows per lane at a time -- probes the incoming
+// filters in probe order (shared memory when they fit, else L1/L2), and
+// writes the survivors' ids into backward segment s (same geometry).  The
+// rows of segment s are the bitmap words of segment s, which only this
+// warp touches: it zero-fills them, then ORs in its survivors, one atomicOr
+// per word run of 32 listed rows.
+//
+// Sector accounting equals a scan's: listed rows are in ascending order, so
+// a stage's sectors are the rows alive at that stage whose sector differs
+// from the previous such row's (segments hold whole sectors).
+// ---------------------------------------------------------------------------
+namespace {
+// Sectors of this group of 32 ascending rows: each live row whose sector
+// (row >> sh0, and row >> sh1 for a second column) differs from that of the
+// previous live row -- in this group, else `last` -- counts.  Returns the
+// last live row (every lane calls it).
+__device__ __forceinline__ uint32_t group_sectors(bool live, uint32_t r, uint32_t sh0, uint32_t sh1, int ncols,
+                                                  uint32_t last, unsigned long long& cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, live);
+    const uint32_t below = m & ((1u << lane) - 1u);
+    const uint32_t pr = __shfl_sync(0xFFFFFFFFu, r, below ? 31 - __clz(below) : 0);
+    const uint32_t prev = below ? pr : last;
+    if (live) {
+        cnt += (r >> sh0) != (prev >> sh0);
+        if (ncols == 2) cnt += (r >> sh1) != (prev >> sh1);
+    }
+    const uint32_t top = __shfl_sync(0xFFFFFFFFu, r, m ? 31 - __clz(m) : 0);
+    return m ? top : last;
+}
+__device__ __forceinline__ uint32_t sector_shift(int32_t dtype) { return dtype == 0 ? 3u : 2u; }
+}  // namespace
+
+template <int B, int KT>
+__global__ void __launch_bounds__(kListThreads, kListMinBlocks)
+    pt_probe_list_kernel(const VisitArgs a, const FilterCfg f) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ ScanShared sh;
+    __shared__ uint32_t s_last[kListThreads / 32][kMaxIn + 1];  // per warp: last row of each stage; [kMaxIn]: survivors
+    constexpr uint32_t WPB = B / 32;
+    constexpr int R = kListRows;
+    const uint32_t FULL = 0xFFFFFFFFu;
+    constexpr uint32_t kNoRow = 0xFFFFFFFFu;  // rows are below 2^31
+
+    if (threadIdx.x == 0) {
+        int ord[kMaxIn];
+        const int m = lip_order(a, -1, ord);
+        sh.n_in = m;
+        int32_t used = 0;
+        for (int i = 0; i < m; ++i) {
+            sh.pe[i] = a.in[ord[i]];
+            const uint32_t nb = (uint32_t)*sh.pe[i].nblocks;
+            sh.nb[i] = nb;
+            sh.split[i] = 0;
+            const int64_t words = (int64_t)nb * WPB;
+            if (used + words <= a.smem_words) {
+                sh.off[i] = used;
+                used += (int32_t)words;
+            } else {
+                sh.off[i] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    const int n_in = sh.n_in;
+    for (int i = 0; i < n_in; ++i)
+        if (sh.off[i] >= 0)
+            copy_to_smem(reinterpret_cast<uint4*>(smem + sh.off[i]), reinterpret_cast<const uint4*>(sh.pe[i].filter),
+                         sh.nb[i] * (WPB / 4));
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t* last = s_last[warp];
+    const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);
+    const int64_t n_words = (a.n + 31) >> 5;
+    const size_t seg_rows = (size_t)a.words_per_warp * 32;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int k = f.k;
+    unsigned long long psec = 0, bsec = 0;  // per lane; reduced at the end
+    uint32_t total = 0;                     // warp-uniform
+
+    for (int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; seg < a.total_warps; seg += W) {
+        // the segment's output words: zero, then OR in the survivors below
+        const int64_t w0 = seg * a.words_per_warp, w1 = min(n_words, w0 + a.words_per_warp);
+        for (int64_t w = w0 + lane; w < w1; w += 32) a.out_bits[w] = 0u;
+        if (lane <= (uint32_t)kMaxIn) last[lane] = kNoRow;
+        __syncwarp();
+        const uint32_t cnt = a.list_seg[seg];
+        const size_t slot0 = (size_t)seg * seg_rows;
+        const uint32_t* ids = a.list_ids + slot0;
+        uint32_t ocnt = 0;  // warp-uniform
+        for (uint32_t b = 0; b < cnt; b += 32u * R) {
+            uint32_t r[R];
+            bool live[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const uint32_t idx = b + lane + 32u * i;
+                live[i] = idx < cnt;
+                r[i] = live[i] ? __ldg(ids + idx) : kNoRow;
+            }
+            for (int s = 0; s < n_in; ++s) {
+                const ProbeEdge& pe = sh.pe[s];
+                const uint64_t* hin = pe.hin + slot0;
+                uint64_t h[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) h[i] = live[i] ? __ldg(reinterpret_cast<const unsigned long long*>(hin) + b + lane + 32u * i) : 0ull;
+                // key sectors of the rows that reach this stage
+                const uint32_t sh0 = sector_shift(pe.col[0].dtype), sh1 = sector_shift(pe.col[1].dtype);
+                uint32_t lr = last[s];
+#pragma unroll
+                for (int i = 0; i < R; ++i) lr = group_sectors(live[i], r[i], sh0, sh1, pe.ncols, lr, psec);
+                __syncwarp();
+                if (lane == 0) last[s] = lr;
+                bool pass[R];
+                if (sh.off[s] >= 0) {
+                    probe_shared_n<B, KT, R>(sfilt + 4u * (uint32_t)sh.off[s], sh.nb[s], h, k, pass);
+                } else {
+                    probe_global_live<B, KT, R>(pe.filter, sh.nb[s], h, k, live, pass);
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) live[i] = live[i] && pass[i];
+            }
+            // survivors: ids into the backward segment, bits into the bitmap,
+            // build-column sectors
+            uint32_t lb = last[kMaxIn];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const uint32_t m = __ballot_sync(FULL, live[i]);
+                if (a.ids && live[i]) a.ids[slot0 + ocnt + __popc(m & lt_mask)] = r[i];
+                ocnt += __popc(m);
+                // word runs: rows ascend across lanes, so equal words are adjacent
+                const uint32_t wd = r[i] >> 5;
+                uint32_t val = live[i] ? 1u << (r[i] & 31) : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v2 = __shfl_down_sync(FULL, val, o);
+                    const uint32_t w2 = __shfl_down_sync(FULL, wd, o);
+                    if (lane + o < 32 && w2 == wd) val |= v2;
+                }
+                const uint32_t wprev = __shfl_up_sync(FULL, wd, 1);
+                if ((lane == 0 || wprev != wd) && val) atomicOr(a.out_bits + wd, val);
+                // build sectors: one count per distinct build column
+                const uint32_t below = m & lt_mask;
+                const uint32_t pr = __shfl_sync(FULL, r[i], below ? 31 - __clz(below) : 0);
+                const uint32_t prev = below ? pr : lb;
+                if (live[i])
+                    for (int c = 0; c < a.n_bcols; ++c) {
+                        const uint32_t shc = sector_shift(a.bcol[c].dtype);
+                        bsec += (r[i] >> shc) != (prev >> shc);
+                    }
+                const uint32_t top = __shfl_sync(FULL, r[i], m ? 31 - __clz(m) : 0);
+                if (m) lb = top;
+            }
+            __syncwarp();
+            if (lane == 0) last[kMaxIn] = lb;
+            __syncwarp();
+        }
+        if (lane == 0 && a.seg_count) a.seg_count[seg] = ocnt;
+        total += ocnt;
+    }
+    psec = __reduce_add_sync(FULL, (unsigned)psec);
+    bsec = __reduce_add_sync(FULL, (unsigned)bsec);
+    if (lane == 0) {
+        if (total) atomicAdd(a.count, (unsigned long long)total);
+        if (psec) atomicAdd(a.stats + 0, psec);
+        if (bsec) atomicAdd(a.stats + 1, bsec);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 2. size + clear the outgoing filters from the device-side survivor count
 // ---------------------------------------------------------------------------
 // Part `part` of `nparts` of a visit's size/clear (thread t of the part zeroes
@@ -1053,6 +1283,13 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
                 uint64_t h[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(be.col[0], be.col[1], be.ncols, r[i], seed) : 0ull;
+                if (be.hout) {
+                    // kept for the backward pass, which probes this edge with the same key
+                    unsigned long long* ho = reinterpret_cast<unsigned long long*>(be.hout) + (size_t)s * seg_rows;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (live[i]) ho[base + lane + 32u * i] = h[i];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (!live[i]) continue;
@@ -1197,6 +1434,29 @@ cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int 
         else pt_insert_kernel<256, 0><<<grid, block, 0, s>>>(a, f);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s) {
+    const int block = kListThreads;
+    if (f.block_bits == 512) {
+        if (f.k == 4) pt_probe_list_kernel<512, 4><<<grid, block, smem, s>>>(a, f);
+        else pt_probe_list_kernel<512, 0><<<grid, block, smem, s>>>(a, f);
+    } else {
+        if (f.k == 4) pt_probe_list_kernel<256, 4><<<grid, block, smem, s>>>(a, f);
+        else pt_probe_list_kernel<256, 0><<<grid, block, smem, s>>>(a, f);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t probe_list_set_smem_limit(int block_bits, size_t smem) {
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (block_bits == 512) {
+        if ((e = cudaFuncSetAttribute(pt_probe_list_kernel<512, 4>, at, (int)smem)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(pt_probe_list_kernel<512, 0>, at, (int)smem);
+    }
+    if ((e = cudaFuncSetAttribute(pt_probe_list_kernel<256, 4>, at, (int)smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pt_probe_list_kernel<256, 0>, at, (int)smem);
 }
 
 int scan_max_ctas_per_sm(int block_bits, int block, size_t smem, bool sparse) {

@@ -62,6 +62,10 @@ struct Visit {
     bool first = false;
     int first_grid = 0;
     size_t first_smem = 0;
+    // a backward visit over the forward survivor list: its launch shape
+    bool list = false;
+    int list_grid = 0;
+    size_t list_smem = 0;
 };
 
 }  // namespace
@@ -84,7 +88,10 @@ struct pt_ctx {
     void* arena = nullptr;
     size_t arena_bytes = 0;
     std::vector<uint32_t*> surv[2];
-    std::vector<uint32_t*> ids, seg;
+    std::vector<uint32_t*> ids[2], seg[2];  // [pass][table]: survivors' row ids in segments, and counts
+    std::vector<uint64_t*> hfwd;            // [edge]: the forward builder's key hash of each of its survivors
+    std::vector<bool> has_edge;             // [table]
+    std::vector<int> vidx[2];               // [pass][table]: index into visits[pass]
     std::vector<uint32_t*> filt[2];
     std::vector<int64_t> filt_max_words;
     unsigned long long* counts[2] = {nullptr, nullptr};  // [table]
@@ -103,6 +110,7 @@ struct pt_ctx {
     int streams = 3;      // visits of a level spread over this many streams (1: one after another)
     int ctas_per_sm = 0;
     int smem_attr_set[2] = {0, 0};
+    int list_attr_set[2] = {0, 0};
     bool shapes_ready = false;
 
     int passes_done = 0;  // bit 0: forward, bit 1: backward
@@ -336,6 +344,10 @@ pt::ColRef colref(const pt_ctx* ctx, int t, int c) {
     return r;
 }
 
+// The arguments of visit `vis` in pass p.  A backward visit in list mode
+// reads the forward survivors' row-id segments (and the hashes the forward
+// inserts stored) instead of a bitmap, in the forward scan's segment
+// geometry, which its own survivor segments keep.
 void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, pt::VisitArgs& a) {
     std::memset(&a, 0, sizeof a);
     const int v = vis.table;
@@ -350,6 +362,15 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     a.total_warps = sh.total_warps;
     a.smem_words = (int32_t)(sh.filter_smem / 4);
     a.cluster = sh.cluster;
+    if (p == 1 && vis.list) {
+        const ScanShape& fs = ctx->visits[0][ctx->vidx[0][v]].shape;
+        a.words_per_warp = fs.words_per_warp;
+        a.total_warps = fs.total_warps;
+        a.smem_words = (int32_t)(vis.list_smem / 4);
+        a.cluster = 1;
+        a.list_ids = ctx->ids[0][v];
+        a.list_seg = ctx->seg[0][v];
+    }
     for (int i = 0; i < a.n_in; ++i) {
         const int e = vis.in_edges[i];
         const pt_edge& ed = ctx->edges[e];
@@ -365,6 +386,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         pe.build_count = ctx->counts[p] + b;
         pe.build_rows = ctx->tables[b].n;
         pe.build_level = ctx->lvl[p][b];
+        if (p == 1 && vis.list) pe.hin = ctx->hfwd[e];
     }
     for (int i = 0; i < a.n_out; ++i) {
         const int e = vis.out_edges[i];
@@ -379,12 +401,15 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         be.filter = ctx->filt[p][e];
         be.nblocks = ctx->nblocks[p] + e;
         be.probe_rows = ctx->tables[other].n;
+        if (p == 0) be.hout = ctx->hfwd[e];
     }
     a.n_bcols = (int)vis.bcols.size();
     for (int i = 0; i < a.n_bcols; ++i) a.bcol[i] = colref(ctx, v, vis.bcols[i]);
-    if (a.n_out > 0) {
-        a.ids = ctx->ids[v];
-        a.seg_count = ctx->seg[v];
+    // every table with an edge keeps its forward survivors' ids (the backward
+    // pass starts from them); backward ids are kept for its builds
+    if (ctx->has_edge[v] && (p == 0 || a.n_out > 0 || vis.list)) {
+        a.ids = ctx->ids[p][v];
+        a.seg_count = ctx->seg[p][v];
     }
 }
 
@@ -404,6 +429,19 @@ pt_status prepare_shapes(pt_ctx* ctx) {
             const bool sparse = p == 1 || ctx->tables[vis.table].sel != nullptr || (vis.first && ctx->first_probe);
             vis.shape = scan_shape(ctx, vis, sparse);
         }
+    if ((int)kScanCtaSmem > ctx->list_attr_set[bi]) {
+        PT_CUDA(ctx, pt::probe_list_set_smem_limit(ctx->fcfg.block_bits, kScanCtaSmem));
+        ctx->list_attr_set[bi] = (int)kScanCtaSmem;
+    }
+    for (Visit& vis : ctx->visits[1]) {
+        if (!vis.list) continue;
+        const ScanShape& fs = ctx->visits[0][ctx->vidx[0][vis.table]].shape;
+        const int64_t want = vis.in_edges.empty() ? 0 : std::min<int64_t>(std::min<int64_t>(ctx->smem_budget, kScanCtaSmem),
+                                                                         vis.max_in_filter_bytes);
+        vis.list_smem = (size_t)(want / 16 * 16);
+        const int wpc = pt::kListThreads / 32;
+        vis.list_grid = std::max(1, (fs.total_warps + wpc - 1) / wpc);
+    }
     for (Visit& vis : ctx->visits[0]) {
         if (!vis.first) continue;
         // the filter budget of one CTA: the largest incoming filter, at most
@@ -488,7 +526,10 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
             a.first_in = ctx->first_idx + v;
         }
         if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
-        PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st));
+        if (p == 1 && vis.list)
+            PT_CUDA(ctx, pt::launch_probe_list(a, ctx->fcfg, vis.list_grid, vis.list_smem, st));
+        else
+            PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st));
         if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
         ctx->launches++;
         if (a.n_out > 0) {
@@ -500,7 +541,7 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
             PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
             // up to three 512-thread CTAs per SM; segments are split between warps when
             // there are more warps than segments
-            const int grid_i = std::max(1, std::min(3 * sh.total_warps / 16 + 1, ctx->num_sms * 3));
+            const int grid_i = std::max(1, std::min(3 * a.total_warps / 16 + 1, ctx->num_sms * 3));
             PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, st));
             if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
             ctx->launches += 2;
@@ -696,6 +737,14 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             ctx->visits[p].push_back(vis);
         }
     }
+    ctx->has_edge.assign(T, false);
+    for (int e = 0; e < E; ++e) ctx->has_edge[ctx->edges[e].t0] = ctx->has_edge[ctx->edges[e].t1] = true;
+    for (int p = 0; p < 2; ++p) {
+        ctx->vidx[p].assign(T, 0);
+        for (int i = 0; i < T; ++i) ctx->vidx[p][ctx->visits[p][i].table] = i;
+    }
+    // a backward visit of a table with an edge starts from its forward survivor list
+    for (Visit& vis : ctx->visits[1]) vis.list = ctx->has_edge[vis.table];
 
     // streams and events for concurrent visits; slot = position of a visit
     // among the visits of its level (level = longest path from a source of
@@ -731,15 +780,16 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
 
     // one device allocation holds every buffer of a run
     ctx->seg_cap = (int64_t)ctx->num_sms * 64;  // at most 64 resident warps per SM
-    std::vector<bool> has_edge(T, false);
-    for (int e = 0; e < E; ++e) has_edge[ctx->edges[e].t0] = has_edge[ctx->edges[e].t1] = true;
+    const std::vector<bool>& has_edge = ctx->has_edge;
     size_t off = 0;
-    std::vector<size_t> o_surv[2], o_ids(T), o_seg(T), o_filt[2], o_mid(T, 0);
+    std::vector<size_t> o_surv[2], o_ids[2], o_seg[2], o_filt[2], o_mid(T, 0), o_hash(E, 0);
     std::vector<bool> has_mid(T, false);
     for (const Visit& vis : ctx->visits[0]) has_mid[vis.table] = vis.first;
     for (int p = 0; p < 2; ++p) {
         o_surv[p].resize(T);
         o_filt[p].resize(E);
+        o_ids[p].resize(T);
+        o_seg[p].resize(T);
     }
     for (int v = 0; v < T; ++v) {
         const size_t wb = (size_t)((n[v] + 31) / 32) * 4;
@@ -747,10 +797,12 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             o_surv[p][v] = off;
             off += align_up(std::max<size_t>(wb, 16));
         }
-        o_ids[v] = off;
-        if (has_edge[v]) off += align_up(std::max<size_t>((size_t)n[v] * 4, 16));
-        o_seg[v] = off;
-        if (has_edge[v]) off += align_up((size_t)ctx->seg_cap * 4);
+        for (int p = 0; p < 2; ++p) {
+            o_ids[p][v] = off;
+            if (has_edge[v]) off += align_up(std::max<size_t>((size_t)n[v] * 4, 16));
+            o_seg[p][v] = off;
+            if (has_edge[v]) off += align_up((size_t)ctx->seg_cap * 4);
+        }
         o_mid[v] = off;  // whole 256-row tiles: the first-probe kernel writes 8 words at a time
         if (has_mid[v]) off += align_up((size_t)((n[v] + 255) / 256) * 32);
     }
@@ -759,6 +811,11 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             o_filt[p][e] = off;
             off += align_up((size_t)ctx->filt_max_words[e] * 4);
         }
+    // per edge: its forward builder's survivors' key hashes, slot-aligned with the ids
+    for (int e = 0; e < E; ++e) {
+        o_hash[e] = off;
+        off += align_up(std::max<size_t>((size_t)n[ctx->src[e]] * 8, 16));
+    }
     // counts [T] u64, stats [T][3] u64, nblocks [E] i64, first-probe edge [T] i32
     ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 24 + (size_t)std::max(E, 1) * 8 + (size_t)T * 4);
     size_t o_meta[2];
@@ -790,12 +847,16 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     ctx->mid.assign(T, nullptr);
     for (int v = 0; v < T; ++v)
         if (has_mid[v]) ctx->mid[v] = (uint32_t*)(base + o_mid[v]);
-    ctx->ids.resize(T);
-    ctx->seg.resize(T);
-    for (int v = 0; v < T; ++v) {
-        ctx->ids[v] = has_edge[v] ? (uint32_t*)(base + o_ids[v]) : nullptr;
-        ctx->seg[v] = has_edge[v] ? (uint32_t*)(base + o_seg[v]) : nullptr;
+    for (int p = 0; p < 2; ++p) {
+        ctx->ids[p].resize(T);
+        ctx->seg[p].resize(T);
+        for (int v = 0; v < T; ++v) {
+            ctx->ids[p][v] = has_edge[v] ? (uint32_t*)(base + o_ids[p][v]) : nullptr;
+            ctx->seg[p][v] = has_edge[v] ? (uint32_t*)(base + o_seg[p][v]) : nullptr;
+        }
     }
+    ctx->hfwd.resize(E);
+    for (int e = 0; e < E; ++e) ctx->hfwd[e] = (uint64_t*)(base + o_hash[e]);
     // bitmaps of tables nobody visits with data still read as zero tails
     PT_CUDA(ctx, cudaMemsetAsync(arena, 0, off, ctx->stream));
     ctx->planned = true;
