@@ -394,6 +394,50 @@ def job_rows_per_s(rows_per_rank: int, world: int, ms: float) -> float:
     return rows_per_rank * world / (ms * 1e-3)
 
 
+def accounting(s, w):
+    """Algorithmic bytes of the session's last run, from every visit's stats:
+    (breakdown, bytes of the scan/list launches, bytes of the first-probe
+    launches).  A first-probe pass reads its key sectors and writes the rows
+    that pass as a bitmap, which the scan kernel reads back as its input."""
+    acc = {"bitmap": 0, "probe_keys": 0, "build_keys": 0, "ids": 0, "filters": 0}
+    scan_bytes = first_bytes = 0
+    for p in range(2):
+        for v, t in enumerate(w.tables):
+            st = s.stats(p, v)
+            nw = (t.n_rows + 31) // 32
+            bm = 4 * nw * (2 if st["has_input_bitmap"] else 1)
+            acc["bitmap"] += bm
+            acc["probe_keys"] += 32 * st["probe_sectors"]
+            acc["build_keys"] += 32 * st["build_sectors"]
+            ids = 8 * st["survivors"] if st["n_out"] > 0 else 0
+            acc["ids"] += ids
+            acc["filters"] += st["filter_bytes"]
+            if st["first_probe"]:
+                first_bytes += 32 * st["first_probe_sectors"] + 4 * nw
+                scan_bytes += bm + 4 * nw + 32 * (st["probe_sectors"] - st["first_probe_sectors"]) + ids // 2
+            else:
+                scan_bytes += bm + 32 * st["probe_sectors"] + ids // 2
+    return acc, scan_bytes, first_bytes
+
+
+def graph_ms(s, stream, steps: int, warmup: int) -> float:
+    """Mean time of one transfer replayed from the session's CUDA graph."""
+    import torch
+    from paper_2307_15255_b300 import pt as P
+    P.pt_set_graph_mode(s.ctx, True)
+    for _ in range(max(warmup, 1)):
+        s.run()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        s.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -446,26 +490,7 @@ def ours(args) -> None:
     # accounting of one run (identical every step: same inputs)
     s.run()
     torch.cuda.synchronize()
-    acc = {"bitmap": 0, "probe_keys": 0, "build_keys": 0, "ids": 0, "filters": 0}
-    # per kernel: a first-probe pass reads its key sectors and writes the rows
-    # that pass as a bitmap, which the scan kernel reads back as its input
-    scan_bytes = first_bytes = 0
-    for p in range(2):
-        for v, t in enumerate(w.tables):
-            st = s.stats(p, v)
-            nw = (t.n_rows + 31) // 32
-            bm = 4 * nw * (2 if st["has_input_bitmap"] else 1)
-            acc["bitmap"] += bm
-            acc["probe_keys"] += 32 * st["probe_sectors"]
-            acc["build_keys"] += 32 * st["build_sectors"]
-            ids = 8 * st["survivors"] if st["n_out"] > 0 else 0
-            acc["ids"] += ids
-            acc["filters"] += st["filter_bytes"]
-            if st["first_probe"]:
-                first_bytes += 32 * st["first_probe_sectors"] + 4 * nw
-                scan_bytes += bm + 4 * nw + 32 * (st["probe_sectors"] - st["first_probe_sectors"]) + ids // 2
-            else:
-                scan_bytes += bm + 32 * st["probe_sectors"] + ids // 2
+    acc, scan_bytes, first_bytes = accounting(s, w)
     alg_bytes = sum(acc.values())
 
     # direct launches (no graph), untimed by kernel events: reported beside the headline
@@ -519,6 +544,22 @@ def ours(args) -> None:
     P.pt_set_kernel_timing(s.ctx, False)
     P.pt_set_graph_mode(s.ctx, False)
 
+    # probe orders (Section 3.2: LIP-style ordering of the incoming filters is
+    # optional): the same survivors; the key sectors read and the step differ.
+    # The LIP order's bytes are the method's own count, the default order's are
+    # what this schedule reads.
+    orders = {}
+    for name, order in (("level_then_lip", 0), ("lip", 1), ("edge_id", 2)):
+        P.pt_set_probe_order(s.ctx, order)
+        s.run()
+        torch.cuda.synchronize()
+        a_o, _, _ = accounting(s, w)
+        ms_o = graph_ms(s, stream, max(5, args.steps // 2), args.warmup)
+        P.pt_set_graph_mode(s.ctx, False)
+        orders[name] = {"order": order, "alg_bytes_per_step": sum(a_o.values()), "ms_per_step": ms_o,
+                        "rows_per_s": rows / (ms_o * 1e-3)}
+    P.pt_set_probe_order(s.ctx, 0)
+
     # end to end through the C ABI from pinned host buffers: H2D of every
     # column and selection, both passes, D2H of every final survivor bitmap
     e2e = None
@@ -553,6 +594,23 @@ def ours(args) -> None:
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n_e2e}
 
     s.close()
+    # the same snowflake at 8 bits per key (the configuration's other swept size)
+    bpk_sweep = {}
+    if not args.no_bpk_sweep:
+        for bpk in (8, 16):
+            if bpk == w.bits_per_key:
+                continue
+            sb = TransferSession(tables_dev, edges, bpk, w.k, w.block_bits, w.seed, stream=stream,
+                                 launch=tuple(tuned["launch"]) if tuned else launch, first_probe=first)
+            sb.run()
+            torch.cuda.synchronize()
+            a_b, _, _ = accounting(sb, w)
+            ms_b = graph_ms(sb, stream, args.steps, args.warmup)
+            sb.close()
+            bpk_sweep[f"bits_per_key_{bpk}"] = {
+                "ms_per_step": ms_b, "value": rows / (ms_b * 1e-3), "unit": "rows/s",
+                "alg_bytes_per_step": sum(a_b.values()),
+                "alg_gbs": sum(a_b.values()) / (ms_b * 1e-3) / 1e9}
     del tables_dev
     torch.cuda.empty_cache()
     serving = None
@@ -564,6 +622,8 @@ def ours(args) -> None:
         return
 
     peak, peak_kind = hbm_peak()
+    for v in bpk_sweep.values():
+        v["frac_of_peak"] = v["alg_gbs"] / peak
     # one replay: one scan per visit, one first-probe pass per visit that has one
     kernels = []
     for name, nbytes, kms, nl in (("pt_probe_first_kernel", first_bytes, kt["first_ms"], kt["first_launches"]),
@@ -573,7 +633,8 @@ def ours(args) -> None:
         per_ms = kms / nl
         ach = (nbytes / nl) / (per_ms * 1e-3) / 1e9
         kernels.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                        "launches_of": ("pt_scan_kernel and pt_scan_sparse_kernel (visits with an input bitmap)"
+                        "launches_of": ("pt_scan_kernel, pt_scan_sparse_kernel (forward visits with an input bitmap) "
+                                        "and pt_probe_list_kernel (backward visits)"
                                         if name == "pt_scan_kernel" else name),
                         "frac": ach / peak, "peak_kind": peak_kind,
                         "traffic": committed_traffic(name, args.workload, args.bpk),
@@ -597,9 +658,14 @@ def ours(args) -> None:
         "hbm": {"alg_bytes_per_step": alg_bytes, "alg_breakdown": acc,
                 "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9,
                 "frac_of_peak": alg_bytes / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak, "peak_kind": peak_kind,
-                "frac_of_nominal_8tbs": alg_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
+                "frac_of_nominal_8tbs": alg_bytes / (ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                # the method's own byte count (LIP probe order) over the same step
+                "alg_bytes_lip_order": orders["lip"]["alg_bytes_per_step"],
+                "frac_of_peak_lip_order_bytes": orders["lip"]["alg_bytes_per_step"] / (ms * 1e-3) / 1e9 / peak},
         "roofline": roof,
         "roofline_kernels": kernels,
+        "probe_orders": orders,
+        "bpk_sweep": bpk_sweep,
         "build_ms_per_step": kt["build_ms"],
         "launch_timeline": timeline,
         "mode": "CUDA graph replay (direct launches: see direct_ms_per_step)",
@@ -634,6 +700,7 @@ def main() -> None:
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-first-probe", action="store_true", help="keep every probe in the scan kernel")
+    ap.add_argument("--no-bpk-sweep", action="store_true", help="skip the other bits-per-key size")
     ap.add_argument("--serving-scale", type=float, default=1.0, help="star size (1 = fact 100M rows)")
     ap.add_argument("--serving-queries", type=int, default=2000)
     ap.add_argument("--serving-single", type=int, default=200, help="queries timed one at a time")

@@ -216,6 +216,27 @@ pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
  * keeps every probe in the scan kernel.  Takes effect at the next run. */
 pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable);
 
+/* Order in which a visit probes its incoming filters (Section 3.2,
+ * "Transfer Schedule": LIP-style ordering of the incoming filters is an
+ * optional optimization).  PT_ORDER_LEVEL_LIP (default): ascending level of
+ * the building visit in the pass's DAG, then ascending c_b / n_b (the
+ * building visit's survivors over its table's rows), then edge id -- the
+ * first filter then exists early, so a first-probe pass can start before
+ * the visit's higher-level builders finish.  PT_ORDER_LIP: c_b / n_b, then
+ * edge id.  PT_ORDER_EDGE: edge id (unordered).  Survivors and filters never
+ * depend on it; the key sectors a visit reads (pt_visit_stats) do.  Takes
+ * effect at the next run. */
+enum { PT_ORDER_LEVEL_LIP = 0, PT_ORDER_LIP = 1, PT_ORDER_EDGE = 2 };
+pt_status pt_set_probe_order(pt_ctx* ctx, int32_t order);
+
+/* CTAs per SM of a first-probe pass (1..3; 0 = as many as fit, the
+ * default).  A first-probe pass over a large table keeps its CTAs resident
+ * until it ends; with fewer per SM, the kernels of the visits that run
+ * beside it (every kernel of a visit fits in the room one first-probe CTA
+ * leaves) start on the same SMs instead of waiting for it.  Results do not
+ * depend on it.  Takes effect at the next run; invalidates a captured graph. */
+pt_status pt_set_first_probe_ctas(pt_ctx* ctx, int32_t ctas_per_sm);
+
 /* Streams the visits of one DAG level are spread over: 1..3 (default 3,
  * visits of a level and a first-probe pass beside its visit's builders run
  * concurrently).  1 runs every launch one after another on one stream, so

@@ -52,7 +52,7 @@ class _Edge(C.Structure):
 
 class _Cfg(C.Structure):
     _fields_ = [("bits_per_key", C.c_int32), ("k", C.c_int32), ("block_bits", C.c_int32),
-                ("pad_", C.c_int32), ("seed", C.c_uint64)]
+                ("probe_order", C.c_int32), ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -184,7 +184,8 @@ def max_filter_words(n0: int, n1: int, bits_per_key: int, block_bits: int) -> in
 
 # ---- the whole transfer ----------------------------------------------------
 
-def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 1) -> Dict[str, list]:
+def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 1,
+             probe_order: int = 0) -> Dict[str, list]:
     """Forward + backward predicate transfer over workload ``w``.
 
     Returns ``surv[p][v]`` (uint32 bitmaps), ``count[p][v]``,
@@ -192,6 +193,8 @@ def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 
     ``sectors[p][v] = (probe_sectors, build_sectors)``; ``p`` is 0 for the
     forward pass and 1 for the backward pass.  ``threads`` > 1 runs the
     OpenMP build of the same source (identical results; timing only).
+    ``probe_order`` 0/1/2: builder level then LIP, LIP, or edge id (only
+    the sector counts depend on it).
     """
     L = lib() if threads <= 1 else lib_threads(threads)[0]
     nt, ne = w.n_tables, len(w.edges)
@@ -216,7 +219,7 @@ def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 
     ea = (_Edge * max(ne, 1))()
     for i, e in enumerate(w.edges):
         _fill_edge(ea[i], e)
-    cfg = _Cfg(w.bits_per_key, w.k, w.block_bits, 0, w.seed if seed is None else seed)
+    cfg = _Cfg(w.bits_per_key, w.k, w.block_bits, probe_order, w.seed if seed is None else seed)
     surv = [[np.zeros((t.n_rows + 31) // 32, np.uint32) for t in w.tables] for _ in range(2)]
     surv_ptrs = (C.c_void_p * (2 * nt))(*[s.ctypes.data for p in surv for s in p])
     count = np.zeros(2 * nt, np.int64)

@@ -41,8 +41,10 @@
  *           visit (its longest path from a source of the pass's DAG, so
  *           filters that are finished earlier come first), then ascending
  *           c_b / n_b (survivors of the building visit over its table's
- *           rows, the LIP-style ordering of Section 3.2), then edge id; the
- *           order never changes a result, only how many key sectors are read.
+ *           rows, the LIP-style ordering of Section 3.2), then edge id
+ *           (probe_order 0); probe_order 1 leaves out the level, 2 is edge
+ *           id alone.  The order never changes a result, only how many key
+ *           sectors are read.
  *
  * Threads: built plainly (liboracle.so) every loop runs on one thread.  The
  * same source built with -fopenmp (liboracle_omp.so, timing only) splits
@@ -72,7 +74,7 @@ typedef struct {
 
 typedef struct {
     int32_t bits_per_key, k, block_bits;
-    int32_t pad_;
+    int32_t probe_order;  /* 0: builder level, LIP, edge id; 1: LIP, edge id; 2: edge id */
     uint64_t seed;
 } o_cfg;
 
@@ -243,6 +245,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
 
     if (B != 256 && B != 512) return -1;
     if (K < 1 || K > 16 || cfg->bits_per_key < 1) return -1;
+    if (cfg->probe_order < 0 || cfg->probe_order > 2) return -1;
     for (i = 0; i < n_edges; i++) {
         if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return -1;
         if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return -1;
@@ -285,16 +288,18 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
                 }
             }
             lvl[p * n_tables + v] = lv;
-            /* probe order: builder level, then LIP ratio, then edge id */
+            /* probe order: builder level (order 0 only), then LIP ratio (orders
+               0 and 1), then edge id */
             for (i = 1; i < n_in; i++) {
                 int32_t x = ine[i];
                 j = i - 1;
                 while (j >= 0) {
                     int32_t y = ine[j];
                     int32_t bx = p == 0 ? src[x] : dst[x], by = p == 0 ? src[y] : dst[y];
-                    int32_t lx = lvl[p * n_tables + bx], ly = lvl[p * n_tables + by];
-                    uint64_t lhs = (uint64_t)count[p * n_tables + bx] * (uint64_t)n_rows[by];
-                    uint64_t rhs = (uint64_t)count[p * n_tables + by] * (uint64_t)n_rows[bx];
+                    int32_t lx = cfg->probe_order == 0 ? lvl[p * n_tables + bx] : 0;
+                    int32_t ly = cfg->probe_order == 0 ? lvl[p * n_tables + by] : 0;
+                    uint64_t lhs = cfg->probe_order == 2 ? 0 : (uint64_t)count[p * n_tables + bx] * (uint64_t)n_rows[by];
+                    uint64_t rhs = cfg->probe_order == 2 ? 0 : (uint64_t)count[p * n_tables + by] * (uint64_t)n_rows[bx];
                     if (lx < ly || (lx == ly && (lhs < rhs || (lhs == rhs && x < y)))) { ine[j + 1] = ine[j]; j--; }
                     else break;
                 }

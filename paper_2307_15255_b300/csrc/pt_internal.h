@@ -81,7 +81,8 @@ struct FilterCfg {
     int32_t bits_per_key;
     int32_t k;
     int32_t block_bits;
-    int32_t pad;
+    int32_t probe_order;  // order of a visit's incoming probes: 0 = builder level, then LIP, then
+                          // edge id; 1 = LIP, then edge id; 2 = edge id (results never depend on it)
     uint64_t seed;
 };
 

@@ -301,14 +301,16 @@ struct ScanShared {
     int32_t n_in;            // edges this kernel probes (a first-probe pass may have taken one)
 };
 
-// Probe order: incoming edges by ascending level of the building visit (its
-// longest path from a source of the pass's DAG: filters finished earlier come
-// first), then ascending survivors/rows of the building visit (LIP-style),
-// then edge id, with in[skip] left out (skip < 0: none).  Writes the in[]
-// indexes to ord and returns their number.  One thread.  The first edge
-// depends only on the counts of the lowest-level builders, so it can be taken
-// while higher-level builders still run.
-__device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord) {
+// Probe order (mode 0, the default): incoming edges by ascending level of the
+// building visit (its longest path from a source of the pass's DAG: filters
+// finished earlier come first), then ascending survivors/rows of the building
+// visit (LIP-style, Section 3.2 "Transfer Schedule"), then edge id.  Mode 1
+// leaves the level out (the LIP ratio, then edge id); mode 2 is edge id alone
+// (unordered).  in[skip] is left out (skip < 0: none).  Writes the in[]
+// indexes to ord and returns their number.  One thread.  In mode 0 the first
+// edge depends only on the counts of the lowest-level builders, so it can be
+// taken while higher-level builders still run.
+__device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int mode, int* ord) {
     unsigned long long c[kMaxIn];
     int m = 0;
 #pragma unroll
@@ -321,9 +323,9 @@ __device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int* ord)
         int j = i - 1;
         while (j >= 0) {
             const int y = ord[j];
-            const int32_t lx = a.in[x].build_level, ly = a.in[y].build_level;
-            const unsigned long long lhs = c[x] * (unsigned long long)a.in[y].build_rows;
-            const unsigned long long rhs = c[y] * (unsigned long long)a.in[x].build_rows;
+            const int32_t lx = mode == 0 ? a.in[x].build_level : 0, ly = mode == 0 ? a.in[y].build_level : 0;
+            const unsigned long long lhs = mode == 2 ? 0ull : c[x] * (unsigned long long)a.in[y].build_rows;
+            const unsigned long long rhs = mode == 2 ? 0ull : c[y] * (unsigned long long)a.in[x].build_rows;
             if (lx < ly || (lx == ly && (lhs < rhs || (lhs == rhs && a.in[x].edge_id < a.in[y].edge_id)))) {
                 ord[j + 1] = ord[j];
                 --j;
@@ -356,7 +358,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
 
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        const int m = lip_order(a, a.first_in ? *a.first_in : -1, ord);
+        const int m = lip_order(a, a.first_in ? *a.first_in : -1, f.probe_order, ord);
         sh.n_in = m;
         // Shared-memory placement, greedily in probe order: a whole copy in
         // every CTA when it fits, else (in a cluster) 1/C of it in each CTA of
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
     const uint32_t FULL = 0xFFFFFFFFu;
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        lip_order(a, -1, ord);
+        lip_order(a, -1, f.probe_order, ord);
         s_pe = a.in[ord[0]];
         s_nb = (uint32_t)*s_pe.nblocks;
         s_fit = (int64_t)s_nb * WPB <= (int64_t)smem_words;
@@ -1072,7 +1074,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
 
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        const int m = lip_order(a, -1, ord);
+        const int m = lip_order(a, -1, f.probe_order, ord);
         sh.n_in = m;
         int32_t used = 0;
         for (int i = 0; i < m; ++i) {

@@ -99,6 +99,7 @@ struct pt_ctx {
     int32_t* first_idx = nullptr;                        // [table]: edge the first-probe pass tested
     std::vector<uint32_t*> mid;                          // [table]: its survivors, or nullptr
     bool first_probe = true;                             // run first-probe passes where they apply
+    int first_ctas = 0;                                  // first-probe CTAs per SM (0: as many as fit)
     int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
     void* meta[2] = {nullptr, nullptr};
     size_t meta_bytes = 0;
@@ -451,6 +452,7 @@ pt_status prepare_shapes(pt_ctx* ctx) {
         vis.first_smem = (size_t)(want / 16 * 16);
         int fit = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, vis.first_smem);
         if (fit < 1) fit = 1;
+        if (ctx->first_ctas > 0) fit = std::min(fit, ctx->first_ctas);
         const int64_t tiles = (ctx->tables[vis.table].n + pt::kFirstTileRows - 1) / pt::kFirstTileRows;
         const int64_t want_ctas = (tiles + pt::kFirstThreads / 32 - 1) / (pt::kFirstThreads / 32);
         vis.first_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit));
@@ -506,14 +508,16 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         fill_visit_args(ctx, p, vis, sh, a);
         pt_status s1;
         if (p == 0 && vis.first && ctx->first_probe) {
-            // the first probe tests a filter of one of the lowest-level builders:
-            // it waits for those only, on its own stream
+            // in the default probe order the first probe tests a filter of one of
+            // the lowest-level builders: it waits for those only, on its own
+            // stream; in the other orders it may be any builder's
             cudaStream_t fs = ctx->streams > 1 ? ctx->fstream[v] : st;
             PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
             int32_t lmin = INT32_MAX;
             for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->src[e]]);
             for (int e : vis.in_edges)
-                if (ctx->lvl[p][ctx->src[e]] == lmin) PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->src[e]], 0));
+                if (ctx->fcfg.probe_order != 0 || ctx->lvl[p][ctx->src[e]] == lmin)
+                    PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->src[e]], 0));
             if ((s1 = record_event(ctx, 2, fs, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_probe_first(a, ctx->fcfg, ctx->mid[v], ctx->first_idx + v,
                                                 (int32_t)(vis.first_smem / 4), vis.first_grid, pt::kFirstThreads,
@@ -539,10 +543,10 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
             int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
             if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
-            // up to three 512-thread CTAs per SM; segments are split between warps when
-            // there are more warps than segments
-            const int grid_i = std::max(1, std::min(3 * a.total_warps / 16 + 1, ctx->num_sms * 3));
-            PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 512, st));
+            // 256-thread CTAs (one fits beside two first-probe CTAs), up to six per SM;
+            // segments are split between warps when there are more warps than segments
+            const int grid_i = std::max(1, std::min(3 * a.total_warps / 8 + 1, ctx->num_sms * 6));
+            PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 256, st));
             if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
             ctx->launches += 2;
         }
@@ -1037,6 +1041,31 @@ pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable) {
         ctx->shapes_ready = false;
     }
     ctx->first_probe = enable == 1;
+    return PT_OK;
+}
+
+pt_status pt_set_probe_order(pt_ctx* ctx, int32_t order) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (order < 0 || order > 2) return fail(ctx, PT_ERR_INVALID, "order must be 0, 1 or 2 (got %d)", order);
+    if (ctx->fcfg.probe_order != order && ctx->gexec) {  // captured kernel parameters hold the old order
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->fcfg.probe_order = order;
+    return PT_OK;
+}
+
+pt_status pt_set_first_probe_ctas(pt_ctx* ctx, int32_t ctas_per_sm) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (ctas_per_sm < 0 || ctas_per_sm > 3) return fail(ctx, PT_ERR_INVALID, "ctas_per_sm must be 0..3 (got %d)", ctas_per_sm);
+    if (ctx->first_ctas != ctas_per_sm) {
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        ctx->shapes_ready = false;
+    }
+    ctx->first_ctas = ctas_per_sm;
     return PT_OK;
 }
 

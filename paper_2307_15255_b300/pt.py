@@ -102,6 +102,8 @@ _SIGS = {
     "pt_set_kernel_timing": (C.c_int, [_P, C.c_int32]),
     "pt_set_cluster": (C.c_int, [_P, C.c_int32]),
     "pt_set_first_probe": (C.c_int, [_P, C.c_int32]),
+    "pt_set_first_probe_ctas": (C.c_int, [_P, C.c_int32]),
+    "pt_set_probe_order": (C.c_int, [_P, C.c_int32]),
     "pt_set_streams": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
     "pt_get_launch_times": (C.c_int, [_P, C.c_int32, C.POINTER(pt_launch_time), C.POINTER(C.c_int32)]),
@@ -292,6 +294,17 @@ def pt_set_streams(ctx: int, streams: int) -> None:
 
 def pt_set_first_probe(ctx: int, enable: bool) -> None:
     _check(lib.pt_set_first_probe(ctx, int(enable)), "pt_set_first_probe", ctx)
+
+
+def pt_set_first_probe_ctas(ctx: int, ctas_per_sm: int) -> None:
+    _check(lib.pt_set_first_probe_ctas(ctx, int(ctas_per_sm)), "pt_set_first_probe_ctas", ctx)
+
+
+PT_ORDER_LEVEL_LIP, PT_ORDER_LIP, PT_ORDER_EDGE = 0, 1, 2
+
+
+def pt_set_probe_order(ctx: int, order: int) -> None:
+    _check(lib.pt_set_probe_order(ctx, int(order)), "pt_set_probe_order", ctx)
 
 
 def pt_get_launch_count(ctx: int) -> int:

@@ -38,7 +38,8 @@ class TransferSession:
                  edges: Sequence[tuple], bits_per_key: int = 10, k: int = 4, block_bits: int = 256,
                  seed: int = 0, stream: Optional[torch.cuda.Stream] = None,
                  launch: Optional[Tuple[int, int, int]] = None, graph: bool = False,
-                 cluster: Optional[int] = None, first_probe: Optional[bool] = None):
+                 cluster: Optional[int] = None, first_probe: Optional[bool] = None,
+                 probe_order: Optional[int] = None):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.block_bits = block_bits
         self.bits_per_key = bits_per_key
@@ -68,6 +69,8 @@ class TransferSession:
                 _pt.pt_set_cluster(self.ctx, cluster)
             if first_probe is not None:
                 _pt.pt_set_first_probe(self.ctx, first_probe)
+            if probe_order is not None:
+                _pt.pt_set_probe_order(self.ctx, probe_order)
             self.order, self.mem_bytes = _pt.pt_plan(self.ctx, len(self.n_rows))
             if graph:
                 _pt.pt_set_graph_mode(self.ctx, True)

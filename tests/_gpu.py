@@ -25,9 +25,11 @@ def edges_of(w):
     return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1)) for e in w.edges]
 
 
-def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None, first_probe=None):
+def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None, first_probe=None,
+                probe_order=None):
     return TransferSession(device_tables(w, host, pin), edges_of(w), w.bits_per_key, w.k, w.block_bits,
-                           w.seed, launch=launch, graph=graph, cluster=cluster, first_probe=first_probe)
+                           w.seed, launch=launch, graph=graph, cluster=cluster, first_probe=first_probe,
+                           probe_order=probe_order)
 
 
 def collect(s, w):

@@ -197,3 +197,58 @@ def test_chain3_exact_magnitudes(oracle_lib):
     assert 1180 < c[2] < 1350
     bl = oracle_lib.transfer(w)
     assert all(bl["count"][1][v] >= c[v] for v in range(3))
+
+
+def _levels_workload():
+    B0 = W.Table("B0", 4, [np.arange(4, dtype=np.int32)], ["k"], W.bitmap_from_rows(4, [0]))
+    A = W.Table("A", 8, [np.arange(8, dtype=np.int32)], ["k"], W.bitmap_from_rows(8, [0, 1, 2, 3]))
+    i16 = np.arange(16, dtype=np.int32)
+    B1 = W.Table("B1", 16, [i16 % 4, i16], ["b0", "bv"], None)
+    i64 = np.arange(64, dtype=np.int32)
+    V = W.Table("V", 64, [i64 // 8, i64 % 16], ["k_a", "k_b"], None)
+    return W.Workload("levels", [B0, A, B1, V],
+                      [W.Edge(1, (0,), 3, (0,)), W.Edge(0, (0,), 2, (0,)), W.Edge(2, (1,), 3, (1,))])
+
+
+@pytest.mark.parametrize("order,sectors", [(0, 8 + 4), (1, 8 + 8), (2, 8 + 4)])
+def test_probe_order_modes_levels_example(oracle_lib, order, sectors):
+    """The example above under each probe order.  LIP alone (order 1) probes
+    B1's filter (rate 4/16) before A's (4/8): B1 passes V's rows with
+    row % 16 in {0, 4, 8, 12}, two in every 8-row sector, so both columns are
+    read in all 8 sectors.  Edge-id order (2) probes edge 0 (A's) first, as
+    the level order does.  The survivors never change."""
+    res = oracle_lib.transfer(_levels_workload(), exact=True, probe_order=order)
+    assert res["sectors"][0][3] == (sectors, 0)
+    assert W.rows_from_bitmap(res["surv"][0][3], 64).tolist() == list(range(0, 32, 4))
+
+
+@pytest.mark.parametrize("order,sectors", [(0, 8 + 1), (1, 8 + 1), (2, 8 + 8)])
+def test_probe_order_modes_edge_id_example(oracle_lib, order, sectors):
+    """The LIP example with Q's edge listed first.  Both builders are on
+    level 0; LIP (orders 0 and 1) still probes P's filter (rate 1/8) first:
+    8 + 1 sectors.  Edge-id order probes Q's filter (rate 1) first, which
+    keeps every row (8 sectors of V.k_q), then P's over all 8 sectors of V.k_p."""
+    P = W.Table("P", 8, [np.arange(8, dtype=np.int32)], ["k"], W.bitmap_from_rows(8, [0]))
+    Q = W.Table("Q", 4, [np.arange(4, dtype=np.int32)], ["k"], None)
+    kp = np.repeat(np.arange(8, dtype=np.int32), 8)
+    kq = (np.arange(64) % 4).astype(np.int32)
+    V = W.Table("V", 64, [kp, kq], ["k_p", "k_q"], None)
+    w = W.Workload("lip_rev", [P, Q, V], [W.Edge(1, (0,), 2, (1,)), W.Edge(0, (0,), 2, (0,))])
+    res = oracle_lib.transfer(w, exact=True, probe_order=order)
+    assert res["sectors"][0][2] == (sectors, 0)
+    assert W.rows_from_bitmap(res["surv"][0][2], 64).tolist() == list(range(8))
+
+
+def test_probe_order_never_changes_results(oracle_lib):
+    for i in range(12):
+        w = W.random_tiny(500 + i, 3 + i % 4, max_rows=200, acyclic=(i % 3 != 0), composite_prob=0.3)
+        base = oracle_lib.transfer(w)
+        for order in (1, 2):
+            got = oracle_lib.transfer(w, probe_order=order)
+            assert got["count"] == base["count"]
+            assert got["nblocks"] == base["nblocks"]
+            for p in range(2):
+                for a, b in zip(got["surv"][p], base["surv"][p]):
+                    assert np.array_equal(a, b)
+                for a, b in zip(got["filters"][p], base["filters"][p]):
+                    assert np.array_equal(a, b)

@@ -44,6 +44,21 @@ def test_cyclic_small(oracle_lib):
     _check(W.cyclic5(scale=0.005), oracle_lib)
 
 
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("make", [
+    # fact table of 1.2M rows: its first probe runs as a pass of its own
+    lambda: W.snowflake(scale=0.2, int64=True, composite=True, zipf=1.1, bits_per_key=16),
+    lambda: W.cyclic5(scale=0.06),
+], ids=["snowflake_x0.2", "cyclic5_x0.06"])
+def test_probe_orders(oracle_lib, order, make):
+    # level-then-LIP, LIP, and edge-id order: the same survivors and filters,
+    # and each order's own sector counts
+    from _gpu import assert_same, run_gpu
+    w = make()
+    got = run_gpu(w, probe_order=order)
+    assert_same(got, oracle_lib.transfer(w, probe_order=order), w)
+
+
 def test_seeded_hash(oracle_lib):
     w = W.chain3(scale=0.3)
     w.seed = 0xDEADBEEF12345678
