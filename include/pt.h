@@ -84,7 +84,15 @@ typedef struct {
 
 /* An equi-join t0.c0[i] = t1.c1[i] for i < ncols (ncols = 1, or 2 for a
  * composite key).  Column indexes refer to pt_register_table's list.
- * flags must be 0 (one-direction edges are not implemented). */
+ * flags: 0, or PT_EDGE_ONE_WAY for the edge of a left outer join t0 LEFT
+ * JOIN t1 (Section 3.4, "Supporting More Operators"): filters flow only from
+ * t0 to t1, so t1 never removes a row of t0.  The edge then transfers in
+ * the one pass that orients it from t0 to t1 (the forward pass when t0 is
+ * the smaller table, else the backward pass) and builds no filter in the
+ * other (pt_get_filter reports 0 blocks there).  A right outer join is the
+ * same edge with t0 and t1 swapped; a full outer join has no edge.  Other
+ * bits are rejected with PT_ERR_UNSUPPORTED. */
+enum { PT_EDGE_ONE_WAY = 1 };
 typedef struct {
     int32_t t0;
     int32_t ncols;

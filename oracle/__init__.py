@@ -32,7 +32,7 @@ _LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 def build(force: bool = False) -> str:
     """Compile pt_oracle.c into liboracle.so next to it (gcc, -O2), and the
     same source with OpenMP into liboracle_omp.so (multi-core timing only)."""
-    for lib_path, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+    for lib_path, extra in ((_LIB, ["-Wno-unknown-pragmas"]), (_LIB_OMP, ["-fopenmp"])):
         if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
             cmd = ["gcc", "-O2", "-std=c11", "-Wall", *extra, "-shared", "-fPIC", "-o", lib_path + ".tmp", _SRC]
             subprocess.check_call(cmd)

@@ -16,6 +16,9 @@
  *   - the schedule (Section 3.2, "Transfer Schedule", Fig. 3): a forward
  *     pass in topological order, then a backward pass over the reversed
  *     edges whose input is the forward survivors;
+ *   - one-direction edges (Section 3.4, outer joins): an edge flagged
+ *     O_EDGE_ONE_WAY transfers only from t0 to t1, so only in the pass that
+ *     orients it that way; in the other pass no filter is built on it;
  *   - "Filter Type" (Section 3.2): with precise filters (exact key sets) a
  *     transfer is a semi-join; mode exact=1 runs that schedule.
  *
@@ -69,8 +72,20 @@ typedef struct {
 
 typedef struct {
     int32_t t0, ncols, c0[2], t1, c1[2];
-    uint32_t flags;
+    uint32_t flags;  /* bit 0: filters flow only from t0 to t1 (Section 3.4: the edge of a
+                        left outer join, t0 the preserved side) */
 } o_edge;
+
+#define O_EDGE_ONE_WAY 1u
+
+/* Is edge i active in pass p?  A pass sends each edge's filter from its
+ * builder (src in the forward pass, dst in the backward pass) to the other
+ * end; a one-way edge only transfers when that builder is its t0, so it is
+ * active in exactly one of the two passes (Section 3.4). */
+static int o_active(const o_edge* e, const int32_t* src, const int32_t* dst, int32_t p, int32_t i) {
+    if (!(e[i].flags & O_EDGE_ONE_WAY)) return 1;
+    return (p == 0 ? src[i] : dst[i]) == e[i].t0;
+}
 
 typedef struct {
     int32_t bits_per_key, k, block_bits;
@@ -229,7 +244,8 @@ static int64_t o_sectors(const unsigned char* flag, int64_t n, int32_t w) {
  * filt[p*n_edges + e]   (Bloom mode; caller-owned, at least
  *                       o_nblocks(min(n_t0, n_t1), ...) * B/32 words):
  *                       the filter built on edge e in pass p.
- * nblocks[p*n_edges+e]: its size in blocks (0 in exact mode).
+ * nblocks[p*n_edges+e]: its size in blocks (0 in exact mode, and for a
+ *                       one-way edge in the pass it is not active in).
  * sectors[(p*n_tables + v)*2 + {0,1}] (nullable): key-column sectors read
  *                       by the probes (each probed column, sectors with a
  *                       row still alive when its edge is probed) and by the
@@ -248,6 +264,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
     if (cfg->probe_order < 0 || cfg->probe_order > 2) return -1;
     for (i = 0; i < n_edges; i++) {
         if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return -1;
+        if (e[i].flags & ~O_EDGE_ONE_WAY) return -1;
         if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return -1;
     }
 
@@ -281,7 +298,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
             int32_t n_in = 0, lv = 0;
             for (i = 0; i < n_edges; i++) {
                 int32_t into = p == 0 ? dst[i] : src[i];
-                if (into == v) {
+                if (into == v && o_active(e, src, dst, p, i)) {
                     int32_t b = p == 0 ? src[i] : dst[i];
                     ine[n_in++] = i;
                     if (lvl[p * n_tables + b] + 1 > lv) lv = lvl[p * n_tables + b] + 1;
@@ -344,7 +361,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
             int32_t n_seen = 0;
             for (i = 0; i < n_edges; i++) {
                 int32_t from = p == 0 ? src[i] : dst[i];
-                if (from != v) continue;
+                if (from != v || !o_active(e, src, dst, p, i)) continue;
                 const o_edge* ed = &e[i];
                 const int32_t* cs;
                 o_side(ed, v, &cs);

@@ -1,4 +1,4 @@
-"""Launch-shape autotuner for a transfer.
+"""Autotuner for a transfer: launch shapes, and filter size and blocking.
 
 The scan kernel's best shape depends on the data: how large the incoming
 filters turn out to be (they are sized on the device from survivor
@@ -9,13 +9,22 @@ CTA, shared-memory filter budget) and keeps the fastest.  Results are
 cached in a JSON file keyed by the workload's shape (row counts, key
 dtypes, join graph, filter parameters), so a later session on the same
 shape reuses them without timing.
+
+:func:`tune_filter` picks the filter parameters themselves -- bits per key
+(the filter's size for a given survivor count), block bits (256 or 512)
+and k -- by timing the same transfer under each candidate.  Unlike a launch
+shape these change the filters and so the survivors (a smaller filter lets
+more non-matching keys through, which the later visits then carry), so the
+result is a configuration to create sessions with, not a setting applied
+to an existing one; the transfer with it is checked like any other
+configuration.
 """
 from __future__ import annotations
 
 import hashlib
 import json
 import os
-from typing import Dict, Iterable, Optional, Sequence, Tuple
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 import torch
 
@@ -35,7 +44,7 @@ def default_cache_path() -> str:
 def signature(session) -> str:
     """A stable key for the session's workload shape."""
     desc = {"n_rows": session.n_rows, "dtypes": session.col_dtypes,
-            "edges": [[e[0], list(e[1]), e[2], list(e[3])] for e in session.edges],
+            "edges": [[e[0], list(e[1]), e[2], list(e[3])] + list(e[4:]) for e in session.edges],
             "cfg": [session.bits_per_key, session.k, session.block_bits],
             "device": torch.cuda.get_device_name()}
     return hashlib.sha256(json.dumps(desc, sort_keys=True).encode()).hexdigest()[:24]
@@ -95,3 +104,38 @@ def tune(session, candidates: Optional[Iterable[Tuple[int, int, int]]] = None, w
         except OSError:
             pass
     return {"launch": best[0], "ms": best[1], "trials": trials, "cached": False}
+
+
+# (bits per key, block bits, k)
+FILTER_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
+    (16, 256, 4), (12, 256, 4), (8, 256, 4), (16, 512, 4), (10, 512, 4), (16, 256, 5),
+)
+
+
+def tune_filter(tables, edges, seed: int = 0, candidates: Optional[Iterable[Tuple[int, int, int]]] = None,
+                stream=None, launch_candidates: Optional[Sequence[Tuple[int, int, int]]] = None,
+                first_probe: Optional[bool] = None, warmup: int = 2, runs: int = 5) -> Dict[str, object]:
+    """Time the transfer of ``tables`` / ``edges`` (as for
+    :class:`~paper_2307_15255_b300.session.TransferSession`) under each
+    filter configuration (bits per key, block bits, k) and return the
+    fastest: {"bits_per_key", "block_bits", "k", "launch", "ms", "trials"}.
+    With ``launch_candidates``, each configuration also gets its best
+    launch shape (:func:`tune`).  Each trial records the survivors left
+    after both passes, summed over the tables."""
+    from .session import TransferSession
+    trials: List[Dict[str, object]] = []
+    for bpk, block_bits, k in (candidates or FILTER_CANDIDATES):
+        with TransferSession(tables, edges, bpk, k, block_bits, seed, stream=stream,
+                             first_probe=first_probe) as s:
+            launch = None
+            if launch_candidates:
+                launch = tune(s, launch_candidates, warmup=warmup, runs=runs, use_cache=False)["launch"]
+            _pt.pt_set_graph_mode(s.ctx, True)
+            ms = _time_graph(s, warmup, runs)
+            survivors = sum(_pt.pt_get_survivors(s.ctx, v, None) for v in range(len(s.n_rows)))
+            trials.append({"bits_per_key": bpk, "block_bits": block_bits, "k": k,
+                           "launch": None if launch is None else list(launch), "ms": ms,
+                           "survivors": survivors})
+    best = min(trials, key=lambda t: t["ms"])
+    return {"bits_per_key": best["bits_per_key"], "block_bits": best["block_bits"], "k": best["k"],
+            "launch": best["launch"], "ms": best["ms"], "trials": trials}

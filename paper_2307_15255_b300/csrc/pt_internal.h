@@ -63,6 +63,7 @@ struct ProbeEdge {
     int32_t pad;
     const uint64_t* hin;                      // backward list probe: this edge's key hash of every
                                               // listed survivor (slot-aligned with list_ids), or nullptr
+                                              // (the list kernel then gathers and hashes the keys)
 };
 
 // An outgoing edge: the visit's key column(s) and the filter it builds.

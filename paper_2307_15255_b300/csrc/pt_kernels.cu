@@ -1025,8 +1025,10 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
 // survived its forward visit (Section 3.2, "Transfer Schedule").  So the
 // filters a table probes in the backward pass are on exactly the edges it
 // built in the forward pass, and the forward insert stored, beside each
-// survivor's row id, the hash of its key on each of those edges.  This
-// kernel therefore reads no key column and no input bitmap: warp w walks
+// survivor's row id, the hash of its key on each of those edges (a one-way
+// edge, which builds in one pass only, is the exception: its keys are
+// gathered and hashed here).  This kernel therefore reads no input bitmap,
+// and no key column for the other edges: warp w walks
 // forward segment s = w, w + W, ... -- row ids and hashes in coalesced 4-
 // and 8-byte loads, kListRows per lane at a time -- probes the incoming
 // filters in probe order (shared memory when they fit, else L1/L2), and
@@ -1132,10 +1134,15 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
             }
             for (int s = 0; s < n_in; ++s) {
                 const ProbeEdge& pe = sh.pe[s];
-                const uint64_t* hin = pe.hin + slot0;
                 uint64_t h[R];
+                if (pe.hin) {  // the hashes the forward insert stored
+                    const unsigned long long* hin = reinterpret_cast<const unsigned long long*>(pe.hin) + slot0;
 #pragma unroll
-                for (int i = 0; i < R; ++i) h[i] = live[i] ? __ldg(reinterpret_cast<const unsigned long long*>(hin) + b + lane + 32u * i) : 0ull;
+                    for (int i = 0; i < R; ++i) h[i] = live[i] ? __ldg(hin + b + lane + 32u * i) : 0ull;
+                } else {       // an edge the forward pass did not build on (one-way): gather and hash
+#pragma unroll
+                    for (int i = 0; i < R; ++i) h[i] = live[i] ? edge_hash(pe.col[0], pe.col[1], pe.ncols, r[i], f.seed) : 0ull;
+                }
                 // key sectors of the rows that reach this stage
                 const uint32_t sh0 = sector_shift(pe.col[0].dtype), sh1 = sector_shift(pe.col[1].dtype);
                 uint32_t lr = last[s];

@@ -183,7 +183,7 @@ pt_status check_edges(pt_ctx* ctx, int32_t n_tables, const std::vector<int>& n_c
     if (n_edges > 0 && !e) return fail(ctx, PT_ERR_INVALID, "edges is NULL");
     for (int i = 0; i < n_edges; ++i) {
         const pt_edge& x = e[i];
-        if (x.flags != 0) return fail(ctx, PT_ERR_UNSUPPORTED, "edge %d: flags 0x%x (one-direction edges) not implemented", i, x.flags);
+        if (x.flags & ~(uint32_t)PT_EDGE_ONE_WAY) return fail(ctx, PT_ERR_UNSUPPORTED, "edge %d: unknown flags 0x%x", i, x.flags);
         if (x.ncols < 1 || x.ncols > 2) return fail(ctx, PT_ERR_INVALID, "edge %d: ncols %d", i, x.ncols);
         if (x.t0 < 0 || x.t0 >= n_tables || x.t1 < 0 || x.t1 >= n_tables)
             return fail(ctx, PT_ERR_INVALID, "edge %d: table id out of range", i);
@@ -387,7 +387,8 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         pe.build_count = ctx->counts[p] + b;
         pe.build_rows = ctx->tables[b].n;
         pe.build_level = ctx->lvl[p][b];
-        if (p == 1 && vis.list) pe.hin = ctx->hfwd[e];
+        // stored by the forward insert, unless this one-way edge built nothing forward
+        if (p == 1 && vis.list && !((ed.flags & PT_EDGE_ONE_WAY) && ctx->src[e] != ed.t0)) pe.hin = ctx->hfwd[e];
     }
     for (int i = 0; i < a.n_out; ++i) {
         const int e = vis.out_edges[i];
@@ -719,6 +720,8 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             for (int e = 0; e < E; ++e) {
                 const int into = p == 0 ? ctx->dst[e] : ctx->src[e];
                 const int from = p == 0 ? ctx->src[e] : ctx->dst[e];
+                // a one-way edge transfers only from its t0 (Section 3.4): in one pass
+                if ((ctx->edges[e].flags & PT_EDGE_ONE_WAY) && from != ctx->edges[e].t0) continue;
                 if (into == vis.table) {
                     vis.in_edges.push_back(e);
                     vis.max_in_filter_bytes += ctx->filt_max_words[e] * 4;

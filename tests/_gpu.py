@@ -22,7 +22,7 @@ def device_tables(w, host=False, pin=False):
 
 
 def edges_of(w):
-    return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1)) for e in w.edges]
+    return [(e.t0, tuple(e.c0), e.t1, tuple(e.c1), e.flags) for e in w.edges]
 
 
 def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None, first_probe=None,

@@ -59,8 +59,10 @@ def test_plan_graph_rejects_malformed_graphs(P):
         P.pt_plan_graph([10, 20], [(0, (0,), 5, (0,))])          # unknown table
     assert ei.value.status == P.PT_ERR_INVALID
     with pytest.raises(P.PtError) as ei:
-        P.pt_plan_graph([10, 20], [(0, (0,), 1, (0,), 1)])      # one-direction edge flag
+        P.pt_plan_graph([10, 20], [(0, (0,), 1, (0,), 2)])      # unknown edge flag
     assert ei.value.status == P.PT_ERR_UNSUPPORTED
+    # a one-direction (left outer join) edge is accepted and oriented like any other
+    assert P.pt_plan_graph([10, 20], [(1, (0,), 0, (0,), 1)])["src"] == [0]
 
 
 @pytest.mark.parametrize("make", [W.chain3, lambda: W.snowflake(scale=0.01), lambda: W.cyclic5(scale=0.001)])

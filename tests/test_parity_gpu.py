@@ -59,6 +59,33 @@ def test_probe_orders(oracle_lib, order, make):
     assert_same(got, oracle_lib.transfer(w, probe_order=order), w)
 
 
+def _one_way(w, idx):
+    import dataclasses
+    return dataclasses.replace(w, edges=[dataclasses.replace(e, flags=1) if i in idx else e
+                                         for i, e in enumerate(w.edges)])
+
+
+@pytest.mark.parametrize("make", [
+    lambda: _one_way(W.chain3(), {0}),
+    lambda: _one_way(W.chain3(), {0, 1}),
+    # fact table of 1.2M rows (first-probe pass); one edge one-way each way round
+    lambda: _one_way(W.snowflake(scale=0.2, int64=True, composite=True, zipf=1.1, bits_per_key=16), {1, 4}),
+    lambda: _one_way(W.cyclic5(scale=0.02), {0, 3}),
+], ids=["chain3_e0", "chain3_both", "snowflake_x0.2", "cyclic5"])
+def test_one_way_edges(oracle_lib, make):
+    # left-outer-join edges (Section 3.4): each active in one pass only
+    _check(make(), oracle_lib)
+
+
+def test_one_way_edges_random_tiny(oracle_lib):
+    from _gpu import assert_same, run_gpu
+    rng = np.random.default_rng(17)
+    for i in range(16):
+        w = W.random_tiny(1300 + i, 3 + i % 5, max_rows=200, acyclic=(i % 2 == 0), composite_prob=0.3)
+        w = _one_way(w, {j for j in range(len(w.edges)) if rng.random() < 0.5})
+        assert_same(run_gpu(w), oracle_lib.transfer(w), w)
+
+
 def test_seeded_hash(oracle_lib):
     w = W.chain3(scale=0.3)
     w.seed = 0xDEADBEEF12345678
@@ -287,3 +314,23 @@ def test_server_arena_too_large_reports_oom():
     with pytest.raises(P.PtError) as ei:
         P.pt_server_create(arena_bytes=1 << 52)
     assert ei.value.status == P.PT_ERR_OOM
+
+
+def test_filter_tuner_choice_is_exact(oracle_lib):
+    # the tuner times whole transfers under each (bits per key, block bits, k);
+    # the configuration it returns gives the oracle's results for that configuration
+    import dataclasses
+
+    from _gpu import assert_same, device_tables, edges_of, run_gpu
+    from paper_2307_15255_b300 import autotune
+    w = W.snowflake(scale=0.05, int64=True, composite=True, zipf=1.1, bits_per_key=16)
+    r = autotune.tune_filter(device_tables(w), edges_of(w), w.seed, candidates=[(16, 256, 4), (8, 512, 4), (12, 256, 3)],
+                             runs=2)
+    assert len(r["trials"]) == 3 and all(t["ms"] > 0 for t in r["trials"])
+    assert r["ms"] == min(t["ms"] for t in r["trials"])
+    wt = dataclasses.replace(w, bits_per_key=r["bits_per_key"], block_bits=r["block_bits"], k=r["k"])
+    assert_same(run_gpu(wt), oracle_lib.transfer(wt), wt)
+    # and every trial's survivor total is the oracle's for its configuration
+    for t in r["trials"]:
+        wc = dataclasses.replace(w, bits_per_key=t["bits_per_key"], block_bits=t["block_bits"], k=t["k"])
+        assert t["survivors"] == sum(oracle_lib.transfer(wc)["count"][1])

@@ -122,3 +122,27 @@ def test_served_full_size_star_samples(oracle_lib):
         for j, (bm, c) in enumerate(res):
             assert np.array_equal(bm, want["surv"][1][j]), (q.inst_table, j)
             assert c == want["count"][1][j]
+
+
+def test_cyclic_graph_through_batched_launches(oracle_lib):
+    # the cyclic 5-table graph (a triangle plus two pendant tables), several
+    # queries with their own selections in one batch: every visit of a DAG
+    # level of every query runs in the same scan, size/clear and insert launches
+    from paper_2307_15255_b300 import build
+    build.build()
+    w = W.cyclic5(scale=0.05)
+    rng = np.random.default_rng(5)
+    qs = []
+    for i in range(3):
+        sel = [t.sel for t in w.tables]
+        if i > 0:  # other 5% selections on T2 and E
+            for v in (2, 4):
+                n = w.tables[v].n_rows
+                sel[v] = W.bitmap_from_rows(n, rng.choice(n, size=n // 20, replace=False))
+        qs.append(W.Query(list(range(w.n_tables)), sel, list(w.edges)))
+    got = run_server(w, qs, 8, 2, 1 << 30)
+    for q, res in zip(qs, got):
+        want = oracle_lib.transfer(query_workload(w, q))
+        for j, (bm, c) in enumerate(res):
+            assert np.array_equal(bm, want["surv"][1][j]), j
+            assert c == want["count"][1][j]
