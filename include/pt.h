@@ -198,6 +198,22 @@ pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uin
 pt_status pt_get_filter(pt_ctx* ctx, int32_t pass, int32_t edge_id, uint32_t* words_out,
                         int64_t* nblocks_out);
 
+/* Join phase (Section 3.3, "unified query plan": the join runs on the
+ * reduced tables): the number of tuples in the join of every registered
+ * table's survivors after the latest pass (uint64, mod 2^64), counted on
+ * the device without building a tuple.  The join graph must be acyclic (a
+ * forest) and of inner joins: each tree is rooted at its largest table,
+ * and bottom-up each child's rows are summed per key into a device hash
+ * table, by which each parent row's weight is multiplied; a tree's count
+ * is its root's weight sum and the join's is their product.  The transfer
+ * keeps every row that takes part in the join, so this equals the count
+ * over the unreduced selected rows.  Errors: PT_ERR_STATE before a pass
+ * has run; PT_ERR_UNSUPPORTED for a cycle or a one-way edge; PT_ERR_OOM
+ * when the temporary device memory (8 bytes per row plus the hash table)
+ * cannot be allocated; PT_ERR_TIMEOUT if a wait on a hash-table slot runs
+ * out (the kernel then stops; the context stays usable).  Synchronizes. */
+pt_status pt_join_count(pt_ctx* ctx, uint64_t* count_out);
+
 /* Accounting of one visit of the last run of that pass.  Synchronizes. */
 pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_visit_stats* out);
 

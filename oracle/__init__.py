@@ -85,6 +85,8 @@ def _declare(L):
                              C.c_void_p]
     L.o_set_threads.restype = C.c_int
     L.o_set_threads.argtypes = [C.c_int32]
+    L.o_join_count.restype = C.c_int
+    L.o_join_count.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     return L
 
 
@@ -183,6 +185,51 @@ def max_filter_words(n0: int, n1: int, bits_per_key: int, block_bits: int) -> in
 
 
 # ---- the whole transfer ----------------------------------------------------
+
+def _tables(w, keep):
+    ta = (_Table * w.n_tables)()
+    for i, t in enumerate(w.tables):
+        cols = [np.ascontiguousarray(c) for c in t.cols]
+        keep.extend(cols)
+        ptrs = (C.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+        dts = (C.c_int32 * len(cols))(*[_dtype_code(c) for c in cols])
+        keep.extend([ptrs, dts])
+        ta[i].n_rows = t.n_rows
+        ta[i].n_cols = len(cols)
+        ta[i].cols = C.cast(ptrs, C.POINTER(C.c_void_p))
+        ta[i].dtypes = C.cast(dts, C.POINTER(C.c_int32))
+        if t.sel is not None:
+            s = np.ascontiguousarray(t.sel, dtype=np.uint32)
+            keep.append(s)
+            ta[i].sel = s.ctypes.data
+        else:
+            ta[i].sel = None
+    return ta
+
+
+def join_count(w, rows: Optional[List[Optional[np.ndarray]]] = None) -> int:
+    """Size of the join (Section 3.3) of the rows set in ``rows[v]`` (uint32
+    bitmaps; None: the tables' selections) over an acyclic join graph of
+    inner equi-joins, counted by sorting and summing per key (no tuple is
+    built).  Raises ValueError for a cyclic graph or a one-way edge."""
+    L = lib()
+    keep = []
+    ta = _tables(w, keep)
+    ea = (_Edge * max(len(w.edges), 1))()
+    for i, e in enumerate(w.edges):
+        _fill_edge(ea[i], e)
+    if rows is None:
+        rows = [t.sel for t in w.tables]
+    arrs = [None if r is None else np.ascontiguousarray(r, dtype=np.uint32) for r in rows]
+    keep.extend(a for a in arrs if a is not None)
+    ptrs = (C.c_void_p * w.n_tables)(*[None if a is None else a.ctypes.data for a in arrs])
+    out = C.c_uint64()
+    rc = L.o_join_count(w.n_tables, C.addressof(ta), len(w.edges), C.addressof(ea), C.addressof(ptrs),
+                        C.byref(out))
+    if rc != 0:
+        raise ValueError("join count needs an acyclic graph of inner joins" if rc == -2 else "invalid workload")
+    return int(out.value)
+
 
 def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 1,
              probe_order: int = 0) -> Dict[str, list]:

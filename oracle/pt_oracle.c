@@ -404,3 +404,123 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
     free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(ine); free(lvl);
     return 0;
 }
+
+/* ---- join phase: the size of the join (Section 3.3) ------------------- */
+
+typedef struct { uint64_t a, b, w; } o_kw;
+
+static int o_kw_cmp(const void* x, const void* y) {
+    const o_kw* p = (const o_kw*)x;
+    const o_kw* q = (const o_kw*)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return 0;
+}
+
+/*
+ * o_join_count: the number of tuples in the join of the rows of every
+ * table whose bit is set in rows[v] (caller-owned bitmaps, ceil(n_v/32)
+ * words; NULL = every row), for an acyclic join graph (a forest) of inner
+ * equi-joins.  Each tree is rooted at its largest table (ties: higher id),
+ * and in post-order every table's row weight (1 for a set row, else 0) is
+ * multiplied, for each child, by the summed weights of the child's rows
+ * with an equal key on the edge joining them; a tree's count is its root's
+ * weight sum, and the join's is the product over trees.  Returns 0 and the
+ * count (mod 2^64) at *out, -1 on invalid input, -2 if the graph has a cycle
+ * or a one-way edge.
+ */
+int o_join_count(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge* e,
+                 uint32_t* const* rows, uint64_t* out) {
+    int32_t v, i;
+    if (n_tables < 1) return -1;
+    for (i = 0; i < n_edges; i++) {
+        if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return -1;
+        if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return -1;
+        if (e[i].flags) return -2;
+    }
+    /* cycle check (union-find) */
+    int32_t* uf = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_tables);
+    for (v = 0; v < n_tables; v++) uf[v] = v;
+    for (i = 0; i < n_edges; i++) {
+        int32_t a = e[i].t0, b = e[i].t1;
+        while (uf[a] != a) a = uf[a];
+        while (uf[b] != b) b = uf[b];
+        if (a == b) { free(uf); return -2; }
+        uf[a] = b;
+    }
+    /* weights */
+    uint64_t** wt = (uint64_t**)malloc(sizeof(uint64_t*) * (size_t)n_tables);
+    for (v = 0; v < n_tables; v++) {
+        int64_t n = t[v].n_rows;
+        wt[v] = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+        for (int64_t r = 0; r < n; r++)
+            wt[v][r] = (!rows || !rows[v]) ? 1u : (uint64_t)((rows[v][r >> 5] >> (r & 31)) & 1u);
+    }
+    /* roots: the largest table of each component; parent links by DFS */
+    int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_tables);
+    int32_t* pedge = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_tables);
+    int32_t* post = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_tables);
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_tables);
+    unsigned char* seen = (unsigned char*)calloc((size_t)n_tables, 1);
+    int32_t n_post = 0;
+    uint64_t total = 1;
+    for (;;) {
+        int32_t root = -1;
+        for (v = 0; v < n_tables; v++)
+            if (!seen[v] && (root < 0 || t[v].n_rows >= t[root].n_rows)) root = v;
+        if (root < 0) break;
+        /* iterative DFS: order[] lists the tree top-down; reversed it is a post-order */
+        int32_t sp = 0, first = n_post;
+        stack[sp++] = root;
+        seen[root] = 1;
+        parent[root] = -1;
+        pedge[root] = -1;
+        while (sp) {
+            int32_t x = stack[--sp];
+            post[n_post++] = x;
+            for (i = 0; i < n_edges; i++) {
+                int32_t y = e[i].t0 == x ? e[i].t1 : (e[i].t1 == x ? e[i].t0 : -1);
+                if (y < 0 || seen[y]) continue;
+                seen[y] = 1;
+                parent[y] = x;
+                pedge[y] = i;
+                stack[sp++] = y;
+            }
+        }
+        /* children before parents */
+        for (int32_t j = n_post - 1; j > first; j--) {
+            int32_t c = post[j], p = parent[c];
+            const o_edge* ed = &e[pedge[c]];
+            int64_t nc = t[c].n_rows, np = t[p].n_rows, m = 0;
+            o_kw* kw = (o_kw*)malloc(sizeof(o_kw) * (size_t)(nc > 0 ? nc : 1));
+            for (int64_t r = 0; r < nc; r++) {
+                if (!wt[c][r]) continue;
+                o_pair k = o_edge_key(&t[c], ed, c, r);
+                kw[m].a = k.a; kw[m].b = k.b; kw[m].w = wt[c][r];
+                m++;
+            }
+            qsort(kw, (size_t)m, sizeof(o_kw), o_kw_cmp);
+            /* sum the weights of equal keys into the first of each run */
+            int64_t u = 0;
+            for (int64_t r = 0; r < m; r++) {
+                if (u > 0 && kw[u - 1].a == kw[r].a && kw[u - 1].b == kw[r].b) kw[u - 1].w += kw[r].w;
+                else kw[u++] = kw[r];
+            }
+            for (int64_t r = 0; r < np; r++) {
+                if (!wt[p][r]) continue;
+                o_pair k = o_edge_key(&t[p], ed, p, r);
+                o_kw probe = {k.a, k.b, 0};
+                o_kw* hit = u > 0 ? (o_kw*)bsearch(&probe, kw, (size_t)u, sizeof(o_kw), o_kw_cmp) : NULL;
+                wt[p][r] *= hit ? hit->w : 0u;
+            }
+            free(kw);
+        }
+        uint64_t s = 0;
+        for (int64_t r = 0; r < t[root].n_rows; r++) s += wt[root][r];
+        total *= s;
+    }
+    for (v = 0; v < n_tables; v++) free(wt[v]);
+    free(wt); free(uf); free(parent); free(pedge); free(post); free(stack); free(seen);
+    *out = total;
+    return 0;
+}

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpt.so")
-SOURCES = ["pt_kernels.cu", "pt_runtime.cu", "pt_static.cu", "pt_server.cu"]
+SOURCES = ["pt_kernels.cu", "pt_runtime.cu", "pt_static.cu", "pt_server.cu", "pt_join.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

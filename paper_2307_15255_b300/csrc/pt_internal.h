@@ -158,6 +158,28 @@ cudaError_t launch_insert_batch(const VisitArgs* visits, const BatchTask* tasks,
 int scan_batch_max_ctas_per_sm(int block_bits, int block, size_t smem);
 cudaError_t scan_batch_set_smem_limit(int block_bits, size_t smem);
 
+// Join phase: a slot of the device hash table that sums row weights per key
+// (state 0 empty, 1 claimed, 2 ready; zero-filled before a build).
+struct JoinSlot {
+    unsigned long long a, b;  // the key (b = 0 for a one-column key)
+    unsigned long long sum;   // summed weights of the rows with that key
+    unsigned state;
+    unsigned pad;
+};
+// w[r] = bit r of `bits` (n rows).
+cudaError_t launch_join_init(const uint32_t* bits, int64_t n, unsigned long long* w, int num_sms, cudaStream_t s);
+// Sum w over the rows of each key (c0, c1 when ncols == 2) into `table`
+// (mask + 1 slots, a power of two); *err: 1 = a wait on a claimed slot ran
+// out, 2 = the table is full.
+cudaError_t launch_join_build(const ColRef& c0, const ColRef& c1, int32_t ncols, const unsigned long long* w, int64_t n,
+                              JoinSlot* table, uint64_t mask, int32_t* err, int num_sms, cudaStream_t s);
+// w[r] *= the sum under row r's key (0 when absent).
+cudaError_t launch_join_probe(const ColRef& c0, const ColRef& c1, int32_t ncols, unsigned long long* w, int64_t n,
+                              const JoinSlot* table, uint64_t mask, int num_sms, cudaStream_t s);
+// *out += sum of w (out zeroed by the caller).
+cudaError_t launch_join_sum(const unsigned long long* w, int64_t n, unsigned long long* out, int num_sms,
+                            cudaStream_t s);
+
 // Message returned by pt_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);
 

@@ -1215,6 +1215,123 @@ pt_status pt_plan_graph(int32_t n_tables, const int64_t* n_rows, int32_t n_edges
     return PT_OK;
 }
 
+pt_status pt_join_count(pt_ctx* ctx, uint64_t* count_out) {
+    pt_status st = require_plan(ctx);
+    if (st != PT_OK) return st;
+    if (!count_out) return fail(ctx, PT_ERR_INVALID, "count_out is NULL");
+    if (!ctx->passes_done) return fail(ctx, PT_ERR_STATE, "no pass has run");
+    const int p = (ctx->passes_done & 2) ? 1 : 0;  // the latest pass's survivors
+    const int T = (int)ctx->tables.size(), E = (int)ctx->edges.size();
+    // an acyclic graph of inner joins: no one-way edge, no cycle (union-find)
+    std::vector<int> uf(T);
+    for (int v = 0; v < T; ++v) uf[v] = v;
+    auto find = [&](int x) {
+        while (uf[x] != x) x = uf[x] = uf[uf[x]];
+        return x;
+    };
+    for (int e = 0; e < E; ++e) {
+        if (ctx->edges[e].flags) return fail(ctx, PT_ERR_UNSUPPORTED, "join count: edge %d is one-way (outer join)", e);
+        const int a = find(ctx->edges[e].t0), b = find(ctx->edges[e].t1);
+        if (a == b) return fail(ctx, PT_ERR_UNSUPPORTED, "join count: the join graph has a cycle (edge %d)", e);
+        uf[a] = b;
+    }
+    // trees rooted at their largest table (ties: higher id); children before parents
+    std::vector<int> parent(T, -1), pedge(T, -1), order, roots;
+    std::vector<char> seen(T, 0);
+    for (;;) {
+        int root = -1;
+        for (int v = 0; v < T; ++v)
+            if (!seen[v] && (root < 0 || ctx->tables[v].n >= ctx->tables[root].n)) root = v;
+        if (root < 0) break;
+        roots.push_back(root);
+        std::vector<int> stack{root};
+        seen[root] = 1;
+        while (!stack.empty()) {
+            const int x = stack.back();
+            stack.pop_back();
+            order.push_back(x);
+            for (int e = 0; e < E; ++e) {
+                const pt_edge& ed = ctx->edges[e];
+                const int y = ed.t0 == x ? ed.t1 : (ed.t1 == x ? ed.t0 : -1);
+                if (y < 0 || seen[y]) continue;
+                seen[y] = 1;
+                parent[y] = x;
+                pedge[y] = e;
+                stack.push_back(y);
+            }
+        }
+    }
+    // survivor counts size each child's hash table (at most half full)
+    std::vector<unsigned long long> cnt(T);
+    PT_CUDA(ctx, cudaMemcpyAsync(cnt.data(), ctx->counts[p], T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    uint64_t cap = 1024;
+    for (int v = 0; v < T; ++v)
+        if (parent[v] >= 0)
+            while (cap < 2 * cnt[v]) cap <<= 1;
+    std::vector<size_t> wo(T);
+    size_t bytes = 0;
+    for (int v = 0; v < T; ++v) {
+        wo[v] = bytes;
+        bytes += align_up(std::max<size_t>((size_t)ctx->tables[v].n * 8, 16));
+    }
+    const size_t o_table = bytes;
+    bytes += align_up(cap * sizeof(pt::JoinSlot));
+    const size_t o_scalars = bytes;  // err flag, then one sum per root
+    bytes += align_up(16 + 8 * roots.size());
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PT_ERR_OOM, "join count: %zu bytes of device memory", bytes);
+    }
+    char* base = (char*)mem;
+    auto w = [&](int v) { return (unsigned long long*)(base + wo[v]); };
+    pt::JoinSlot* table = (pt::JoinSlot*)(base + o_table);
+    int32_t* err = (int32_t*)(base + o_scalars);
+    unsigned long long* sums = (unsigned long long*)(base + o_scalars + 16);
+    auto run = [&]() -> pt_status {
+        PT_CUDA(ctx, cudaMemsetAsync(base + o_scalars, 0, 16 + 8 * roots.size(), ctx->stream));
+        for (int v = 0; v < T; ++v)
+            PT_CUDA(ctx, pt::launch_join_init(ctx->surv[p][v], ctx->tables[v].n, w(v), ctx->num_sms, ctx->stream));
+        for (size_t i = order.size(); i-- > 0;) {
+            const int c = order[i], par = parent[c];
+            if (par < 0) continue;
+            const pt_edge& ed = ctx->edges[pedge[c]];
+            const int32_t* cc = ed.t0 == c ? ed.c0 : ed.c1;
+            const int32_t* cp = ed.t0 == par ? ed.c0 : ed.c1;
+            uint64_t m = 1024;
+            while (m < 2 * cnt[c]) m <<= 1;
+            PT_CUDA(ctx, cudaMemsetAsync(table, 0, m * sizeof(pt::JoinSlot), ctx->stream));
+            PT_CUDA(ctx, pt::launch_join_build(colref(ctx, c, cc[0]), colref(ctx, c, ed.ncols == 2 ? cc[1] : cc[0]),
+                                               ed.ncols, w(c), ctx->tables[c].n, table, m - 1, err, ctx->num_sms,
+                                               ctx->stream));
+            PT_CUDA(ctx, pt::launch_join_probe(colref(ctx, par, cp[0]), colref(ctx, par, ed.ncols == 2 ? cp[1] : cp[0]),
+                                               ed.ncols, w(par), ctx->tables[par].n, table, m - 1, ctx->num_sms,
+                                               ctx->stream));
+        }
+        for (size_t i = 0; i < roots.size(); ++i)
+            PT_CUDA(ctx, pt::launch_join_sum(w(roots[i]), ctx->tables[roots[i]].n, sums + i, ctx->num_sms, ctx->stream));
+        return PT_OK;
+    };
+    st = run();
+    int32_t herr = 0;
+    std::vector<unsigned long long> hs(roots.size());
+    if (st == PT_OK) {
+        cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(hs.data(), sums, 8 * roots.size(), cudaMemcpyDeviceToHost, ctx->stream);
+        const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PT_ERR_CUDA, "join count: %s", cudaGetErrorString(e));
+    }
+    cudaFree(mem);
+    if (st != PT_OK) return st;
+    if (herr == 1) return fail(ctx, PT_ERR_TIMEOUT, "join count: a wait on a hash-table slot ran out");
+    if (herr) return fail(ctx, PT_ERR_CUDA, "join count: hash table full");
+    uint64_t total = 1;
+    for (unsigned long long x : hs) total *= x;
+    *count_out = total;
+    return PT_OK;
+}
+
 const char* pt_last_error(pt_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"

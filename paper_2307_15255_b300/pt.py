@@ -104,6 +104,7 @@ _SIGS = {
     "pt_set_first_probe": (C.c_int, [_P, C.c_int32]),
     "pt_set_first_probe_ctas": (C.c_int, [_P, C.c_int32]),
     "pt_set_probe_order": (C.c_int, [_P, C.c_int32]),
+    "pt_join_count": (C.c_int, [_P, _P]),
     "pt_set_streams": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
     "pt_get_launch_times": (C.c_int, [_P, C.c_int32, C.POINTER(pt_launch_time), C.POINTER(C.c_int32)]),
@@ -298,6 +299,13 @@ def pt_set_first_probe(ctx: int, enable: bool) -> None:
 
 def pt_set_first_probe_ctas(ctx: int, ctas_per_sm: int) -> None:
     _check(lib.pt_set_first_probe_ctas(ctx, int(ctas_per_sm)), "pt_set_first_probe_ctas", ctx)
+
+
+def pt_join_count(ctx: int) -> int:
+    """Size of the join of the survivors (see include/pt.h)."""
+    n = C.c_uint64()
+    _check(lib.pt_join_count(ctx, C.byref(n)), "pt_join_count", ctx)
+    return n.value
 
 
 PT_ORDER_LEVEL_LIP, PT_ORDER_LIP, PT_ORDER_EDGE = 0, 1, 2

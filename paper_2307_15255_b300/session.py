@@ -121,6 +121,10 @@ class TransferSession:
     def stats(self, pass_: int, table_id: int) -> dict:
         return _pt.pt_get_visit_stats(self.ctx, pass_, table_id)
 
+    def join_count(self) -> int:
+        """Size of the join of the survivors (acyclic graphs of inner joins)."""
+        return _pt.pt_join_count(self.ctx)
+
     def close(self) -> None:
         if self.ctx is not None:
             _pt.pt_destroy(self.ctx)

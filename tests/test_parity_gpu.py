@@ -334,3 +334,60 @@ def test_filter_tuner_choice_is_exact(oracle_lib):
     for t in r["trials"]:
         wc = dataclasses.replace(w, bits_per_key=t["bits_per_key"], block_bits=t["block_bits"], k=t["k"])
         assert t["survivors"] == sum(oracle_lib.transfer(wc)["count"][1])
+
+
+@pytest.mark.parametrize("make", [
+    W.chain3,
+    lambda: W.snowflake(scale=0.05, int64=True, composite=True, zipf=1.1, bits_per_key=16),
+], ids=["chain3", "snowflake_x0.05"])
+def test_join_count_on_survivors(oracle_lib, make):
+    # the join phase on the reduced tables equals the oracle's count on the
+    # unreduced selections (the snowflake is cyclic: rejected)
+    from _gpu import session_for
+    w = make()
+    with session_for(w) as s:
+        s.run()
+        try:
+            want = oracle_lib.join_count(w)
+        except ValueError:
+            from paper_2307_15255_b300 import pt as P
+            with pytest.raises(P.PtError) as ei:
+                s.join_count()
+            assert ei.value.status == P.PT_ERR_UNSUPPORTED
+            return
+        assert s.join_count() == want
+
+
+def test_join_count_random_trees(oracle_lib):
+    from _gpu import session_for
+    for seed in range(12):
+        w = W.random_tiny(2200 + seed, 2 + seed % 5, max_rows=300, domain=8, acyclic=True, composite_prob=0.3)
+        with session_for(w) as s:
+            s.run()
+            assert s.join_count() == oracle_lib.join_count(w), seed
+
+
+def test_join_count_star_forest_and_one_way(oracle_lib):
+    import dataclasses
+
+    from _gpu import session_for
+    from paper_2307_15255_b300 import pt as P
+    # a star with a selective predicate on each dimension, plus a disconnected
+    # pair of tables: a forest, whose count is the product of its trees'
+    w = W.star(scale=0.003, bits_per_key=12)
+    rng = np.random.default_rng(9)
+    tabs = [w.tables[0]] + [dataclasses.replace(t, sel=W.bitmap_from_rows(t.n_rows, rng.choice(
+        t.n_rows, size=max(1, t.n_rows // 5), replace=False))) for t in w.tables[1:]]
+    extra = W.random_tiny(31, 2, max_rows=50, domain=5)
+    k = len(tabs)
+    w2 = W.Workload("forest", tabs + extra.tables,
+                    w.edges + [dataclasses.replace(e, t0=e.t0 + k, t1=e.t1 + k) for e in extra.edges])
+    with session_for(w2) as s:
+        s.run()
+        assert s.join_count() == oracle_lib.join_count(w2)
+    w3 = dataclasses.replace(w2, edges=[dataclasses.replace(w2.edges[0], flags=1)] + w2.edges[1:])
+    with session_for(w3) as s:
+        s.run()
+        with pytest.raises(P.PtError) as ei:
+            s.join_count()
+        assert ei.value.status == P.PT_ERR_UNSUPPORTED
