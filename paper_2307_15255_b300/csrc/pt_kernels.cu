@@ -518,25 +518,38 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
 #pragma unroll
             for (int i = 0; i < R; ++i) emit(pass[i], r[i]);
         } else {
-            // the rest of the queue (cnt < kDrain is the whole queue): 32 rows at a time
-            for (uint32_t b = 0; b < cnt; b += 32) {
-                const uint32_t idx = b + lane;
-                const bool live = idx < cnt;
-                const uint32_t r = live ? q[idx] : 0u;
-                bool pass = false;
-                if (live) {
-                    count_sectors(r, idx == 0 ? prev0 : q[idx - 1]);
-                    const uint64_t h = edge_hash(c0, c1, ncols, r, seed);
-                    pass = off < 0   ? probe_global<B, KT>(fg, nb, h, k)
-                           : split ? probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h, k)
-                                   : probe_shared<B, KT>(sfilt + 4u * (uint32_t)off, nb, h, k);
-                }
-                emit(pass, r);
+            // the rest of the queue (cnt < kDrain is the whole queue): one batch
+            // with the lanes past its end idle, so that its gathers are in flight
+            // together rather than one 32-row group after another
+            constexpr int R = kDrain / 32;
+            uint32_t r[R];
+            bool live[R];
+            uint64_t h[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const uint32_t idx = lane + 32u * i;
+                live[i] = idx < cnt;
+                r[i] = live[i] ? q[idx] : 0u;
+                if (live[i]) count_sectors(r[i], idx == 0 ? prev0 : q[idx - 1]);
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) h[i] = live[i] ? edge_hash(c0, c1, ncols, r[i], seed) : 0ull;
+            bool pass[R];
+            if (off >= 0 && !split) {
+                probe_shared_n<B, KT, R>(sfilt + 4u * (uint32_t)off, nb, h, k, pass);
+            } else if (off >= 0) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    pass[i] = live[i] && probe_cluster<B, KT>(sfilt + 4u * (uint32_t)off, lc, nb, h[i], k);
+            } else {
+                probe_global_live<B, KT, R>(fg, nb, h, k, live, pass);
             }
             const uint32_t last_row = q[cnt - 1];
             __syncwarp();
             if (lane == 0) last_in[s] = last_row;
             qset(s, 0u);
+#pragma unroll
+            for (int i = 0; i < R; ++i) emit(pass[i] && live[i], r[i]);
         }
         if (!last) qset(s + 1, nn);
         __syncwarp();
