@@ -394,9 +394,10 @@ pt_status pt_server_destroy(pt_server* srv);
  * that cannot allocate device memory: engines that give all device memory
  * to their own pool up front, paths where an allocation (which can
  * synchronize the device) is not acceptable, and services that must not
- * meet an out-of-memory error in the middle of a query.  pt_visit_static runs one filter transformation (Section 3.2, Fig.
- * 2) -- probe, survivor bitmap, compaction, size/clear and insert -- with
- * every input and output supplied by the caller.  Its scratch (compacted
+ * meet an out-of-memory error in the middle of a query.  pt_visit_static
+ * runs one visit of a table -- probe, survivor bitmap, compaction,
+ * size/clear and insert -- with every input and output supplied by the
+ * caller.  Its scratch (compacted
  * row ids, per-warp segment lengths, counters) is a fixed array of about
  * 4.1 MB that is part of the library's device image: every GPU that loads
  * the library holds it until the process exits, and nothing is allocated
