@@ -132,8 +132,13 @@ struct BatchTask {
 // its key sectors to a.stats[2] and a.stats[0].  The filter is copied into
 // shared memory when it fits smem_words; smem is the dynamic shared memory
 // of the launch (>= smem_words * 4).
+// gate 0 runs always; gate 1 only if the filter fits gate_words, gate 2 only
+// if it does not (a pair of launches, with and without the shared-memory
+// budget, of which exactly one does the work: a filter that cannot fit
+// leaves the whole L1 to the probes through it).
 cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t* mid, int32_t* first,
-                               int32_t smem_words, int grid, int block, size_t smem, cudaStream_t s);
+                               int32_t smem_words, int32_t gate_words, int32_t gate, int grid, int block,
+                               size_t smem, cudaStream_t s);
 int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem);
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s);

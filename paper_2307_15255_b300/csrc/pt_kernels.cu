@@ -307,15 +307,18 @@ struct ScanShared {
 // visit (LIP-style, Section 3.2 "Transfer Schedule"), then edge id.  Mode 1
 // leaves the level out (the LIP ratio, then edge id); mode 2 is edge id alone
 // (unordered).  in[skip] is left out (skip < 0: none).  Writes the in[]
-// indexes to ord and returns their number.  One thread.  In mode 0 the first
-// edge depends only on the counts of the lowest-level builders, so it can be
-// taken while higher-level builders still run.
-__device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int mode, int* ord) {
+// indexes to ord and returns their number; nbs[i] receives in[i]'s filter
+// size in blocks (every count and size is loaded at once: one round trip).
+// One thread.  In mode 0 the first edge depends only on the counts of the
+// lowest-level builders, so it can be taken while higher-level builders
+// still run (their sizes are then not read by the caller).
+__device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int mode, int* ord, uint32_t* nbs) {
     unsigned long long c[kMaxIn];
     int m = 0;
 #pragma unroll
     for (int i = 0; i < kMaxIn; ++i) {
         c[i] = i < a.n_in ? *a.in[i].build_count : 0ull;
+        nbs[i] = i < a.n_in ? (uint32_t)*a.in[i].nblocks : 0u;
         if (i < a.n_in && i != skip) ord[m++] = i;
     }
     for (int i = 1; i < m; ++i) {
@@ -358,7 +361,8 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
 
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        const int m = lip_order(a, a.first_in ? *a.first_in : -1, f.probe_order, ord);
+        uint32_t nbs[kMaxIn];
+        const int m = lip_order(a, a.first_in ? *a.first_in : -1, f.probe_order, ord, nbs);
         sh.n_in = m;
         // Shared-memory placement, greedily in probe order: a whole copy in
         // every CTA when it fits, else (in a cluster) 1/C of it in each CTA of
@@ -368,7 +372,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         for (int i = 0; i < m; ++i) {
             const ProbeEdge& pe = a.in[ord[i]];
             s_pe[i] = pe;
-            const uint32_t nb = (uint32_t)*pe.nblocks;
+            const uint32_t nb = nbs[ord[i]];
             s_nb[i] = nb;
             s_split[i] = 0;
             const int64_t words = (int64_t)nb * WPB;
@@ -893,23 +897,28 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
 template <int B, int KT>
 __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
     pt_probe_first_kernel(const VisitArgs a, const FilterCfg f, uint32_t* __restrict__ mid, int32_t* first,
-                          const int32_t smem_words) {
+                          const int32_t smem_words, const int32_t gate_words, const int32_t gate) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ProbeEdge s_pe;
     __shared__ uint32_t s_nb;
-    __shared__ int32_t s_fit;
+    __shared__ int32_t s_fit, s_run;
     constexpr uint32_t WPB = B / 32;
     constexpr int R = kFirstTileRows / 32;  // rows per lane of a tile
     const uint32_t FULL = 0xFFFFFFFFu;
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        lip_order(a, -1, f.probe_order, ord);
+        uint32_t nbs[kMaxIn];
+        lip_order(a, -1, f.probe_order, ord, nbs);
         s_pe = a.in[ord[0]];
-        s_nb = (uint32_t)*s_pe.nblocks;
+        s_nb = nbs[ord[0]];
         s_fit = (int64_t)s_nb * WPB <= (int64_t)smem_words;
-        if (blockIdx.x == 0) *first = ord[0];
+        // gate 1: run only if the filter fits gate_words; 2: only if it does not
+        const bool fits = (int64_t)s_nb * WPB <= (int64_t)gate_words;
+        s_run = gate == 0 || (gate == 1) == fits;
+        if (blockIdx.x == 0 && s_run) *first = ord[0];
     }
     __syncthreads();
+    if (!s_run) return;  // the other launch of the pair has this filter
     const uint32_t nb = s_nb;
     const bool in_smem = s_fit != 0;
     if (in_smem) {
@@ -1089,12 +1098,13 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
 
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
-        const int m = lip_order(a, -1, f.probe_order, ord);
+        uint32_t nbs[kMaxIn];
+        const int m = lip_order(a, -1, f.probe_order, ord, nbs);
         sh.n_in = m;
         int32_t used = 0;
         for (int i = 0; i < m; ++i) {
             sh.pe[i] = a.in[ord[i]];
-            const uint32_t nb = (uint32_t)*sh.pe[i].nblocks;
+            const uint32_t nb = nbs[ord[i]];
             sh.nb[i] = nb;
             sh.split[i] = 0;
             const int64_t words = (int64_t)nb * WPB;
@@ -1419,13 +1429,14 @@ cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int bl
 }
 
 cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t* mid, int32_t* first,
-                               int32_t smem_words, int grid, int block, size_t smem, cudaStream_t s) {
+                               int32_t smem_words, int32_t gate_words, int32_t gate, int grid, int block,
+                               size_t smem, cudaStream_t s) {
     if (f.block_bits == 512) {
-        if (f.k == 4) pt_probe_first_kernel<512, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
-        else pt_probe_first_kernel<512, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+        if (f.k == 4) pt_probe_first_kernel<512, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words, gate_words, gate);
+        else pt_probe_first_kernel<512, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words, gate_words, gate);
     } else {
-        if (f.k == 4) pt_probe_first_kernel<256, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
-        else pt_probe_first_kernel<256, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words);
+        if (f.k == 4) pt_probe_first_kernel<256, 4><<<grid, block, smem, s>>>(a, f, mid, first, smem_words, gate_words, gate);
+        else pt_probe_first_kernel<256, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words, gate_words, gate);
     }
     return cudaGetLastError();
 }
