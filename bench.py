@@ -492,6 +492,7 @@ def ours(args) -> None:
     torch.cuda.synchronize()
     acc, scan_bytes, first_bytes = accounting(s, w)
     alg_bytes = sum(acc.values())
+    pt_survivors = [s.survivors(v)[1] for v in range(w.n_tables)]
 
     # direct launches (no graph), untimed by kernel events: reported beside the headline
     for _ in range(max(args.warmup, 0)):
@@ -559,6 +560,27 @@ def ours(args) -> None:
         orders[name] = {"order": order, "alg_bytes_per_step": sum(a_o.values()), "ms_per_step": ms_o,
                         "rows_per_s": rows / (ms_o * 1e-3)}
     P.pt_set_probe_order(s.ctx, 0)
+
+    # the Bloom join (Section 2.1; the BloomJoin baseline of Section 4) on the
+    # same tables: every filter built from its table's selection, probed once.
+    # What the join phase would get from each schedule, and each one's step.
+    one_hop = None
+    if not args.no_one_hop:
+        so = TransferSession(tables_dev, edges, w.bits_per_key, w.k, w.block_bits, w.seed, stream=stream,
+                             launch=tuple(tuned["launch"]) if tuned else launch, first_probe=first,
+                             schedule=P.PT_SCHEDULE_ONE_HOP)
+        so.run()
+        torch.cuda.synchronize()
+        oh_survivors = [so.survivors(v)[1] for v in range(w.n_tables)]
+        ms_oh = graph_ms(so, stream, args.steps, args.warmup)
+        so.close()
+        one_hop = {
+            "ms_per_step": ms_oh, "rows_per_s": rows / (ms_oh * 1e-3),
+            "survivors": {t.name: c for t, c in zip(w.tables, oh_survivors)},
+            "transfer_survivors": {t.name: c for t, c in zip(w.tables, pt_survivors)},
+            "join_input_rows": sum(oh_survivors), "transfer_join_input_rows": sum(pt_survivors),
+            "join_input_ratio": sum(oh_survivors) / max(1, sum(pt_survivors)),
+        }
 
     # end to end through the C ABI from pinned host buffers: H2D of every
     # column and selection, both passes, D2H of every final survivor bitmap
@@ -665,6 +687,7 @@ def ours(args) -> None:
         "roofline": roof,
         "roofline_kernels": kernels,
         "probe_orders": orders,
+        "one_hop": one_hop,
         "bpk_sweep": bpk_sweep,
         "build_ms_per_step": kt["build_ms"],
         "launch_timeline": timeline,
@@ -698,6 +721,7 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-one-hop", action="store_true", help="skip the one-hop (Bloom join) comparison")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-first-probe", action="store_true", help="keep every probe in the scan kernel")
     ap.add_argument("--no-bpk-sweep", action="store_true", help="skip the other bits-per-key size")

@@ -164,6 +164,28 @@ pt_status pt_set_join_graph(pt_ctx* ctx, int32_t n_edges, const pt_edge* edges);
  * PT_ERR_INVALID. */
 pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out);
 
+/* The schedule pt_plan builds (only before pt_plan).
+ *
+ * PT_SCHEDULE_TRANSFER (default): predicate transfer, a forward and a
+ * backward pass over the transfer DAG (Section 3.2): a table's outgoing
+ * filters hold the keys of the rows that survived its incoming ones.
+ *
+ * PT_SCHEDULE_ONE_HOP: the Bloom join of Section 2.1, a one-hop transfer in
+ * one direction.  Each edge's filter is built from its builder's selected
+ * rows only (its local predicate) and probed by the other end; nothing is
+ * transferred further.  The builder is the edge's smaller table (the DAG's
+ * orientation), or t0 for a PT_EDGE_ONE_WAY edge.  Pass 0 ("forward") builds
+ * every filter: its visits are the tables with an outgoing edge, and their
+ * pass-0 survivors are their selections.  Pass 1 ("backward") probes: every
+ * table starts from its selection and keeps the rows all its incoming
+ * filters accept.  pt_get_survivors returns pass 1's result; pt_get_filter
+ * and pt_get_pass_survivors take pass 0 for what the builders built and
+ * pass 1 for the probes.  Only pt_run_transfer / pt_run_forward /
+ * pt_run_backward follow it (a pt_server always transfers).  Returns
+ * PT_ERR_STATE after pt_plan. */
+enum { PT_SCHEDULE_TRANSFER = 0, PT_SCHEDULE_ONE_HOP = 1 };
+pt_status pt_set_schedule(pt_ctx* ctx, int32_t schedule);
+
 /* Forward pass: visit every table in topological order of the transfer
  * graph; a visit's input is its selection bitmap.  Asynchronous. */
 pt_status pt_run_forward(pt_ctx* ctx);
@@ -188,7 +210,9 @@ pt_status pt_set_graph_mode(pt_ctx* ctx, int32_t on);
  * NULL).  Synchronizes the context's stream. */
 pt_status pt_get_survivors(pt_ctx* ctx, int32_t table_id, uint32_t* bitmap_out, int64_t* count_out);
 
-/* Same for a given pass (0 = forward, 1 = backward). */
+/* Same for a given pass (0 = forward, 1 = backward).  PT_ERR_INVALID for a
+ * table the pass does not visit (pass 0 of PT_SCHEDULE_ONE_HOP visits the
+ * builders only). */
 pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uint32_t* bitmap_out,
                                 int64_t* count_out);
 
@@ -214,7 +238,8 @@ pt_status pt_get_filter(pt_ctx* ctx, int32_t pass, int32_t edge_id, uint32_t* wo
  * out (the kernel then stops; the context stays usable).  Synchronizes. */
 pt_status pt_join_count(pt_ctx* ctx, uint64_t* count_out);
 
-/* Accounting of one visit of the last run of that pass.  Synchronizes. */
+/* Accounting of one visit of the last run of that pass.  PT_ERR_INVALID for
+ * a table the pass does not visit.  Synchronizes. */
 pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_visit_stats* out);
 
 /* Launch shape of the scan kernel: threads per CTA (64..256, multiple of

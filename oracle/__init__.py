@@ -83,6 +83,9 @@ def _declare(L):
     L.o_transfer.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                              C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p]
+    L.o_one_hop.restype = C.c_int
+    L.o_one_hop.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                            C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     L.o_set_threads.restype = C.c_int
     L.o_set_threads.argtypes = [C.c_int32]
     L.o_join_count.restype = C.c_int
@@ -295,6 +298,43 @@ def transfer(w, exact: bool = False, seed: Optional[int] = None, threads: int = 
         "nblocks": [[int(nblocks[p * ne + e]) for e in range(ne)] for p in range(2)],
         "sectors": [[(int(sectors[(p * nt + v) * 2]), int(sectors[(p * nt + v) * 2 + 1]))
                      for v in range(nt)] for p in range(2)],
+    }
+
+
+def one_hop(w, exact: bool = False, seed: Optional[int] = None, threads: int = 1) -> Dict[str, list]:
+    """The Bloom join (Section 2.1): every edge's filter is built from its
+    building table's selected rows (the smaller table, or t0 of a one-way
+    edge) and probed once by the other end.
+
+    Returns ``surv[v]`` (uint32 bitmaps), ``count[v]``, ``filters[e]``
+    (uint32 words, Bloom mode) and ``nblocks[e]``.
+    """
+    L = lib() if threads <= 1 else lib_threads(threads)[0]
+    nt, ne = w.n_tables, len(w.edges)
+    keep = []
+    ta = _tables(w, keep)
+    ea = (_Edge * max(ne, 1))()
+    for i, e in enumerate(w.edges):
+        _fill_edge(ea[i], e)
+    cfg = _Cfg(w.bits_per_key, w.k, w.block_bits, 0, w.seed if seed is None else seed)
+    surv = [np.zeros((t.n_rows + 31) // 32, np.uint32) for t in w.tables]
+    surv_ptrs = (C.c_void_p * max(nt, 1))(*[s.ctypes.data for s in surv])
+    count = np.zeros(max(nt, 1), np.int64)
+    filt = [np.zeros(1 if exact else max_filter_words(w.tables[e.t0].n_rows, w.tables[e.t1].n_rows,
+                                                       w.bits_per_key, w.block_bits), np.uint32)
+            for e in w.edges]
+    filt_ptrs = (C.c_void_p * max(ne, 1))(*[f.ctypes.data for f in filt])
+    nblocks = np.zeros(max(ne, 1), np.int64)
+    rc = L.o_one_hop(nt, C.addressof(ta), ne, C.addressof(ea), C.addressof(cfg), int(exact),
+                     C.addressof(surv_ptrs), count.ctypes.data, C.addressof(filt_ptrs), nblocks.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the workload")
+    wpb = w.block_bits // 32
+    return {
+        "surv": surv,
+        "count": [int(count[v]) for v in range(nt)],
+        "filters": [filt[e][: nblocks[e] * wpb].copy() for e in range(ne)],
+        "nblocks": [int(nblocks[e]) for e in range(ne)],
     }
 
 

@@ -20,7 +20,11 @@
  *     O_EDGE_ONE_WAY transfers only from t0 to t1, so only in the pass that
  *     orients it that way; in the other pass no filter is built on it;
  *   - "Filter Type" (Section 3.2): with precise filters (exact key sets) a
- *     transfer is a semi-join; mode exact=1 runs that schedule.
+ *     transfer is a semi-join; mode exact=1 runs that schedule;
+ *   - the Bloom join (Section 2.1, and the BloomJoin baseline of Section 4),
+ *     a one-hop transfer in one direction: each edge's filter holds the keys
+ *     of its building table's selected rows only and is probed once
+ *     (o_one_hop).
  *
  * The paper fixes no hash, filter layout, filter size or number of bits.
  * This library fixes them as follows (the same definitions, written
@@ -235,6 +239,20 @@ static int64_t o_sectors(const unsigned char* flag, int64_t n, int32_t w) {
     return cnt;
 }
 
+/* filter configuration and edges in range */
+static int o_valid(int32_t n_tables, int32_t n_edges, const o_edge* e, const o_cfg* cfg) {
+    int32_t i;
+    if (cfg->block_bits != 256 && cfg->block_bits != 512) return 0;
+    if (cfg->k < 1 || cfg->k > 16 || cfg->bits_per_key < 1) return 0;
+    if (cfg->probe_order < 0 || cfg->probe_order > 2) return 0;
+    for (i = 0; i < n_edges; i++) {
+        if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return 0;
+        if (e[i].flags & ~O_EDGE_ONE_WAY) return 0;
+        if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return 0;
+    }
+    return 1;
+}
+
 /*
  * o_transfer: the full forward + backward predicate transfer.
  *
@@ -259,14 +277,7 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
     int32_t B = cfg->block_bits, K = cfg->k, wpb = cfg->block_bits / 32;
     int32_t v, p, i, j;
 
-    if (B != 256 && B != 512) return -1;
-    if (K < 1 || K > 16 || cfg->bits_per_key < 1) return -1;
-    if (cfg->probe_order < 0 || cfg->probe_order > 2) return -1;
-    for (i = 0; i < n_edges; i++) {
-        if (e[i].ncols < 1 || e[i].ncols > 2 || e[i].t0 == e[i].t1) return -1;
-        if (e[i].flags & ~O_EDGE_ONE_WAY) return -1;
-        if (e[i].t0 < 0 || e[i].t0 >= n_tables || e[i].t1 < 0 || e[i].t1 >= n_tables) return -1;
-    }
+    if (!o_valid(n_tables, n_edges, e, cfg)) return -1;
 
     int64_t* n_rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_tables > 0 ? n_tables : 1));
     int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
@@ -402,6 +413,100 @@ int o_transfer(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge
     }
     for (i = 0; i < 2 * n_edges; i++) free(set[i]);
     free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(ine); free(lvl);
+    return 0;
+}
+
+/*
+ * o_one_hop: the Bloom join (Section 2.1; the BloomJoin baseline of Section
+ * 4), a one-hop transfer in one direction.  Every edge has one building
+ * table: the smaller one by the transfer graph's orientation (a Bloom join
+ * builds on the smaller table), or t0 for a one-way edge.  Its filter holds
+ * the join keys of the building table's selected rows -- its local predicate
+ * alone, nothing received from another table -- and is sized by the same
+ * rule as a transfer's, with c = the number of selected rows.  A table then
+ * keeps a selected row iff every filter built for it accepts the row's key.
+ *
+ * surv[v] (caller-owned, ceil(n_v/32) words), count[v]: the result per
+ * table.  filt[e] (Bloom mode; caller-owned, as in o_transfer), nblocks[e]:
+ * the filter of edge e (0 blocks in exact mode, where it is the key set).
+ * Returns 0, or -1 on invalid input.
+ */
+int o_one_hop(int32_t n_tables, const o_table* t, int32_t n_edges, const o_edge* e,
+              const o_cfg* cfg, int32_t exact, uint32_t* const* surv, int64_t* count,
+              uint32_t* const* filt, int64_t* nblocks) {
+    int32_t B = cfg->block_bits, K = cfg->k, wpb = cfg->block_bits / 32;
+    int32_t v, i;
+    if (!o_valid(n_tables, n_edges, e, cfg)) return -1;
+
+    int64_t* n_rows = (int64_t*)calloc((size_t)(n_tables > 0 ? n_tables : 1), sizeof(int64_t));
+    int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    int32_t* dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_tables + 1));
+    int32_t* bld = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_edges + 1));
+    o_pair** set = (o_pair**)calloc((size_t)(n_edges + 1), sizeof(o_pair*));
+    int64_t* set_n = (int64_t*)calloc((size_t)(n_edges + 1), sizeof(int64_t));
+    for (v = 0; v < n_tables; v++) n_rows[v] = t[v].n_rows;
+    o_orient(n_tables, n_rows, n_edges, e, src, dst, order);
+
+    /* build: one filter per edge from the building table's selected rows */
+    for (i = 0; i < n_edges; i++) {
+        const o_edge* ed = &e[i];
+        int32_t b = (ed->flags & O_EDGE_ONE_WAY) ? ed->t0 : src[i];
+        int32_t q = b == ed->t0 ? ed->t1 : ed->t0;
+        int64_t n = n_rows[b], c = 0, r;
+        bld[i] = b;
+        for (r = 0; r < n; r++) c += t[b].sel ? o_bit(t[b].sel, r) : 1;
+        if (exact) {
+            o_pair* s = (o_pair*)malloc(sizeof(o_pair) * (size_t)(c > 0 ? c : 1));
+            int64_t m = 0;
+            for (r = 0; r < n; r++)
+                if (!t[b].sel || o_bit(t[b].sel, r)) s[m++] = o_edge_key(&t[b], ed, b, r);
+            qsort(s, (size_t)m, sizeof(o_pair), o_pair_cmp);
+            set[i] = s;
+            set_n[i] = m;
+            nblocks[i] = 0;
+        } else {
+            int64_t nb = o_nblocks(c, n_rows[q], cfg->bits_per_key, B);
+            memset(filt[i], 0, sizeof(uint32_t) * (size_t)(nb * wpb));
+#pragma omp parallel for schedule(static)
+            for (r = 0; r < n; r++)
+                if (!t[b].sel || o_bit(t[b].sel, r)) o_filter_insert(filt[i], nb, B, K, o_edge_hash(&t[b], ed, b, r, cfg->seed));
+            nblocks[i] = nb;
+        }
+    }
+
+    /* probe: a selected row survives iff every filter built for its table accepts its key */
+    for (v = 0; v < n_tables; v++) {
+        int64_t n = n_rows[v], c = 0, w;
+        unsigned char* alive = (unsigned char*)malloc((size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < n; r++) alive[r] = t[v].sel ? (unsigned char)o_bit(t[v].sel, r) : 1;
+        for (i = 0; i < n_edges; i++) {
+            const o_edge* ed = &e[i];
+            if (bld[i] == v || (ed->t0 != v && ed->t1 != v)) continue;
+#pragma omp parallel for schedule(static)
+            for (int64_t r = 0; r < n; r++) {
+                if (!alive[r]) continue;
+                if (exact) {
+                    o_pair key = o_edge_key(&t[v], ed, v, r);
+                    alive[r] = set_n[i] > 0 && bsearch(&key, set[i], (size_t)set_n[i], sizeof(o_pair), o_pair_cmp) != NULL;
+                } else {
+                    alive[r] = (unsigned char)o_filter_probe(filt[i], nblocks[i], B, K, o_edge_hash(&t[v], ed, v, r, cfg->seed));
+                }
+            }
+        }
+#pragma omp parallel for schedule(static) reduction(+ : c)
+        for (w = 0; w < (n + 31) / 32; w++) {
+            uint32_t x = 0;
+            for (int64_t r = 32 * w; r < 32 * w + 32 && r < n; r++)
+                if (alive[r]) { x |= 1u << (r & 31); c++; }
+            surv[v][w] = x;
+        }
+        count[v] = c;
+        free(alive);
+    }
+    for (i = 0; i < n_edges; i++) free(set[i]);
+    free(set); free(set_n); free(n_rows); free(src); free(dst); free(order); free(bld);
     return 0;
 }
 

@@ -88,6 +88,11 @@ struct pt_ctx {
 
     std::vector<int32_t> src, dst, order, level;
     std::vector<Visit> visits[2];
+    int schedule = PT_SCHEDULE_TRANSFER;
+    // [pass][edge]: the table that builds the edge's filter in that pass and
+    // the one that probes it (-1: not built in that pass)
+    std::vector<int32_t> bld[2], prb[2];
+    int fpass[2] = {0, 1};  // the pass whose filters (and builders' counts) pass p probes
 
     void* arena = nullptr;
     size_t arena_bytes = 0;
@@ -358,7 +363,10 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     std::memset(&a, 0, sizeof a);
     const int v = vis.table;
     a.n = ctx->tables[v].n;
-    a.in_bits = p == 0 ? ctx->tables[v].sel : ctx->surv[0][v];
+    // the backward pass of a transfer starts from the forward survivors; every
+    // other visit from the table's selection
+    const bool one_hop = ctx->schedule == PT_SCHEDULE_ONE_HOP;
+    a.in_bits = p == 0 || one_hop ? ctx->tables[v].sel : ctx->surv[0][v];
     a.out_bits = ctx->surv[p][v];
     a.count = ctx->counts[p] + v;
     a.stats = ctx->stats[p] + 3 * v;
@@ -381,17 +389,18 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         const int e = vis.in_edges[i];
         const pt_edge& ed = ctx->edges[e];
         const int32_t* cs = ed.t0 == v ? ed.c0 : ed.c1;
-        const int b = p == 0 ? ctx->src[e] : ctx->dst[e];  // the table that built the filter
+        const int fp = ctx->fpass[p];
+        const int b = ctx->bld[fp][e];  // the table that built the filter
         pt::ProbeEdge& pe = a.in[i];
         pe.ncols = ed.ncols;
         pe.edge_id = e;
         pe.col[0] = colref(ctx, v, cs[0]);
         pe.col[1] = ed.ncols == 2 ? colref(ctx, v, cs[1]) : pe.col[0];
-        pe.filter = ctx->filt[p][e];
-        pe.nblocks = ctx->nblocks[p] + e;
-        pe.build_count = ctx->counts[p] + b;
+        pe.filter = ctx->filt[fp][e];
+        pe.nblocks = ctx->nblocks[fp] + e;
+        pe.build_count = ctx->counts[fp] + b;
         pe.build_rows = ctx->tables[b].n;
-        pe.build_level = ctx->lvl[p][b];
+        pe.build_level = ctx->lvl[fp][b];
         // stored by the forward insert, unless this one-way edge built nothing forward
         if (p == 1 && vis.list && !((ed.flags & PT_EDGE_ONE_WAY) && ctx->src[e] != ed.t0)) pe.hin = ctx->hfwd[e];
     }
@@ -408,7 +417,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         be.filter = ctx->filt[p][e];
         be.nblocks = ctx->nblocks[p] + e;
         be.probe_rows = ctx->tables[other].n;
-        if (p == 0) be.hout = ctx->hfwd[e];
+        if (p == 0 && !one_hop) be.hout = ctx->hfwd[e];
     }
     a.n_bcols = (int)vis.bcols.size();
     for (int i = 0; i < a.n_bcols; ++i) a.bcol[i] = colref(ctx, v, vis.bcols[i]);
@@ -433,7 +442,9 @@ pt_status prepare_shapes(pt_ctx* ctx) {
     }
     for (int p = 0; p < 2; ++p)
         for (Visit& vis : ctx->visits[p]) {
-            const bool sparse = p == 1 || ctx->tables[vis.table].sel != nullptr || (vis.first && ctx->first_probe);
+            // an input bitmap: a transfer's backward visits, a selection, a first-probe pass
+            const bool sparse = (p == 1 && ctx->schedule == PT_SCHEDULE_TRANSFER) ||
+                                ctx->tables[vis.table].sel != nullptr || (vis.first && ctx->first_probe);
             vis.shape = scan_shape(ctx, vis, sparse);
         }
     if ((int)kScanCtaSmem > ctx->list_attr_set[bi]) {
@@ -449,27 +460,28 @@ pt_status prepare_shapes(pt_ctx* ctx) {
         const int wpc = pt::kListThreads / 32;
         vis.list_grid = std::max(1, (fs.total_warps + wpc - 1) / wpc);
     }
-    for (Visit& vis : ctx->visits[0]) {
-        if (!vis.first) continue;
-        // the filter budget of one CTA: the largest incoming filter, at most
-        // the context's budget (a first filter that does not fit is probed from L2)
-        const int64_t want = std::min<int64_t>(std::min<int64_t>(ctx->smem_budget, kFirstCtaSmem),
-                                               vis.max_single_filter_bytes);
-        vis.first_smem = (size_t)(want / 16 * 16);
-        int fit = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, vis.first_smem);
-        if (fit < 1) fit = 1;
-        if (ctx->first_ctas > 0) fit = std::min(fit, ctx->first_ctas);
-        const int64_t tiles = (ctx->tables[vis.table].n + pt::kFirstTileRows - 1) / pt::kFirstTileRows;
-        const int64_t want_ctas = (tiles + pt::kFirstThreads / 32 - 1) / (pt::kFirstThreads / 32);
-        vis.first_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit));
-        vis.first_pair = ctx->first_pair && vis.first_smem > 0 && vis.max_single_filter_bytes > (int64_t)vis.first_smem;
-        if (vis.first_pair) {
-            int fit0 = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, 0);
-            if (fit0 < 1) fit0 = 1;
-            if (ctx->first_ctas > 0) fit0 = std::min(fit0, ctx->first_ctas);
-            vis.first_grid0 = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit0));
+    for (int p = 0; p < 2; ++p)
+        for (Visit& vis : ctx->visits[p]) {
+            if (!vis.first) continue;
+            // the filter budget of one CTA: the largest incoming filter, at most
+            // the context's budget (a first filter that does not fit is probed from L2)
+            const int64_t want = std::min<int64_t>(std::min<int64_t>(ctx->smem_budget, kFirstCtaSmem),
+                                                   vis.max_single_filter_bytes);
+            vis.first_smem = (size_t)(want / 16 * 16);
+            int fit = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, vis.first_smem);
+            if (fit < 1) fit = 1;
+            if (ctx->first_ctas > 0) fit = std::min(fit, ctx->first_ctas);
+            const int64_t tiles = (ctx->tables[vis.table].n + pt::kFirstTileRows - 1) / pt::kFirstTileRows;
+            const int64_t want_ctas = (tiles + pt::kFirstThreads / 32 - 1) / (pt::kFirstThreads / 32);
+            vis.first_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit));
+            vis.first_pair = ctx->first_pair && vis.first_smem > 0 && vis.max_single_filter_bytes > (int64_t)vis.first_smem;
+            if (vis.first_pair) {
+                int fit0 = pt::probe_first_max_ctas_per_sm(ctx->fcfg.block_bits, pt::kFirstThreads, 0);
+                if (fit0 < 1) fit0 = 1;
+                if (ctx->first_ctas > 0) fit0 = std::min(fit0, ctx->first_ctas);
+                vis.first_grid0 = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, (int64_t)ctx->num_sms * fit0));
+            }
         }
-    }
     ctx->shapes_ready = true;
     return PT_OK;
 }
@@ -512,25 +524,28 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         const int v = vis.table;
         cudaStream_t st = ctx->aux[ctx->slot[p][v] % ctx->streams];
         PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
-        for (int e : vis.in_edges) {
-            const int b = p == 0 ? ctx->src[e] : ctx->dst[e];  // the table that built the filter
-            PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[p][b], 0));
-        }
+        // the visits that build its filters in this pass (filters of an earlier
+        // pass are complete when this one forks from the context stream)
+        const bool same_pass = ctx->fpass[p] == p;
+        if (same_pass)
+            for (int e : vis.in_edges) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[p][ctx->bld[p][e]], 0));
         const ScanShape& sh = vis.shape;
         pt::VisitArgs a;
         fill_visit_args(ctx, p, vis, sh, a);
         pt_status s1;
-        if (p == 0 && vis.first && ctx->first_probe) {
+        if (vis.first && ctx->first_probe) {
             // in the default probe order the first probe tests a filter of one of
             // the lowest-level builders: it waits for those only, on its own
             // stream; in the other orders it may be any builder's
             cudaStream_t fs = ctx->streams > 1 ? ctx->fstream[v] : st;
             PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
-            int32_t lmin = INT32_MAX;
-            for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->src[e]]);
-            for (int e : vis.in_edges)
-                if (ctx->fcfg.probe_order != 0 || ctx->lvl[p][ctx->src[e]] == lmin)
-                    PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->src[e]], 0));
+            if (same_pass) {
+                int32_t lmin = INT32_MAX;
+                for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->bld[p][e]]);
+                for (int e : vis.in_edges)
+                    if (ctx->fcfg.probe_order != 0 || ctx->lvl[p][ctx->bld[p][e]] == lmin)
+                        PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->bld[p][e]], 0));
+            }
             // and for the first-probe passes of lower-level visits: those lead to
             // this visit's higher-level builders, and a first-probe pass over a
             // large table holds every SM until it ends (measured on the benchmark:
@@ -742,16 +757,43 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     for (int e = 0; e < E; ++e)
         ctx->filt_max_words[e] = max_filter_words(n[ctx->edges[e].t0], n[ctx->edges[e].t1], f);
 
+    // who builds and who probes each edge's filter in each pass
+    const bool one_hop = ctx->schedule == PT_SCHEDULE_ONE_HOP;
+    for (int p = 0; p < 2; ++p) {
+        ctx->bld[p].assign(E, -1);
+        ctx->prb[p].assign(E, -1);
+    }
+    for (int e = 0; e < E; ++e) {
+        const pt_edge& ed = ctx->edges[e];
+        const bool one_way = (ed.flags & PT_EDGE_ONE_WAY) != 0;
+        if (one_hop) {
+            // a Bloom join (Section 2.1): built in pass 0 from the smaller table's
+            // selection (a one-way edge's t0), probed in pass 1 by the other end
+            const int b = one_way ? ed.t0 : ctx->src[e];
+            ctx->bld[0][e] = b;
+            ctx->prb[1][e] = b == ed.t0 ? ed.t1 : ed.t0;
+        } else {
+            // forward along the DAG, backward against it; a one-way edge transfers
+            // only from its t0 (Section 3.4): in one of the two passes
+            for (int p = 0; p < 2; ++p) {
+                const int from = p == 0 ? ctx->src[e] : ctx->dst[e];
+                if (one_way && from != ed.t0) continue;
+                ctx->bld[p][e] = from;
+                ctx->prb[p][e] = p == 0 ? ctx->dst[e] : ctx->src[e];
+            }
+        }
+    }
+    ctx->fpass[0] = 0;
+    ctx->fpass[1] = one_hop ? 0 : 1;
+
     for (int p = 0; p < 2; ++p) {
         ctx->visits[p].clear();
         for (int oi = 0; oi < T; ++oi) {
             Visit vis;
             vis.table = p == 0 ? ctx->order[oi] : ctx->order[T - 1 - oi];
             for (int e = 0; e < E; ++e) {
-                const int into = p == 0 ? ctx->dst[e] : ctx->src[e];
-                const int from = p == 0 ? ctx->src[e] : ctx->dst[e];
-                // a one-way edge transfers only from its t0 (Section 3.4): in one pass
-                if ((ctx->edges[e].flags & PT_EDGE_ONE_WAY) && from != ctx->edges[e].t0) continue;
+                const int into = ctx->prb[p][e];
+                const int from = ctx->bld[p][e];
                 if (into == vis.table) {
                     vis.in_edges.push_back(e);
                     vis.max_in_filter_bytes += ctx->filt_max_words[e] * 4;
@@ -769,7 +811,13 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                 (int)vis.bcols.size() > pt::kMaxBuildCols)
                 return fail(ctx, PT_ERR_UNSUPPORTED, "table %d has more than %d incoming or %d outgoing edges in a pass",
                             vis.table, pt::kMaxIn, pt::kMaxOut);
-            vis.first = p == 0 && !vis.in_edges.empty() && ctx->tables[vis.table].sel == nullptr &&
+            // the probing pass of a one-hop schedule visits every table (a table
+            // without incoming filters keeps its selection); its building pass only
+            // the builders
+            if (one_hop && p == 0 && vis.out_edges.empty()) continue;
+            // a first-probe pass: the visit's rows all start alive (the forward
+            // pass of a transfer, the probing pass of a one-hop schedule)
+            vis.first = p == (one_hop ? 1 : 0) && !vis.in_edges.empty() && ctx->tables[vis.table].sel == nullptr &&
                         ctx->tables[vis.table].n >= pt::kFirstMinRows;
             ctx->visits[p].push_back(vis);
         }
@@ -777,11 +825,12 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     ctx->has_edge.assign(T, false);
     for (int e = 0; e < E; ++e) ctx->has_edge[ctx->edges[e].t0] = ctx->has_edge[ctx->edges[e].t1] = true;
     for (int p = 0; p < 2; ++p) {
-        ctx->vidx[p].assign(T, 0);
-        for (int i = 0; i < T; ++i) ctx->vidx[p][ctx->visits[p][i].table] = i;
+        ctx->vidx[p].assign(T, -1);
+        for (int i = 0; i < (int)ctx->visits[p].size(); ++i) ctx->vidx[p][ctx->visits[p][i].table] = i;
     }
     // a backward visit of a table with an edge starts from its forward survivor list
-    for (Visit& vis : ctx->visits[1]) vis.list = ctx->has_edge[vis.table];
+    if (!one_hop)
+        for (Visit& vis : ctx->visits[1]) vis.list = ctx->has_edge[vis.table];
 
     // streams and events for concurrent visits; slot = position of a visit
     // among the visits of its level (level = longest path from a source of
@@ -797,8 +846,8 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         lvl.assign(T, 0);
         for (const Visit& vis : ctx->visits[p])
             for (int e : vis.out_edges) {
-                const int to = p == 0 ? ctx->dst[e] : ctx->src[e];
-                lvl[to] = std::max(lvl[to], lvl[vis.table] + 1);
+                const int to = ctx->prb[p][e];
+                if (to >= 0) lvl[to] = std::max(lvl[to], lvl[vis.table] + 1);
             }
         ctx->slot[p].assign(T, 0);
         for (const Visit& vis : ctx->visits[p]) {
@@ -809,11 +858,12 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     }
     ctx->fstream.assign(T, nullptr);
     ctx->fev.assign(T, nullptr);
-    for (const Visit& vis : ctx->visits[0]) {
-        if (!vis.first) continue;
-        PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->fstream[vis.table], cudaStreamNonBlocking));
-        PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fev[vis.table], cudaEventDisableTiming));
-    }
+    for (int p = 0; p < 2; ++p)
+        for (const Visit& vis : ctx->visits[p]) {
+            if (!vis.first) continue;
+            PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->fstream[vis.table], cudaStreamNonBlocking));
+            PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fev[vis.table], cudaEventDisableTiming));
+        }
 
     // one device allocation holds every buffer of a run
     ctx->seg_cap = (int64_t)ctx->num_sms * 64;  // at most 64 resident warps per SM
@@ -821,7 +871,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     size_t off = 0;
     std::vector<size_t> o_surv[2], o_ids[2], o_seg[2], o_filt[2], o_mid(T, 0), o_hash(E, 0);
     std::vector<bool> has_mid(T, false);
-    for (const Visit& vis : ctx->visits[0]) has_mid[vis.table] = vis.first;
+    for (int p = 0; p < 2; ++p)
+        for (const Visit& vis : ctx->visits[p])
+            if (vis.first) has_mid[vis.table] = true;
     for (int p = 0; p < 2; ++p) {
         o_surv[p].resize(T);
         o_filt[p].resize(E);
@@ -988,6 +1040,7 @@ pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uin
     if (pass < 0 || pass > 1) return fail(ctx, PT_ERR_INVALID, "pass %d", pass);
     if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
     if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
+    if (ctx->vidx[pass][table_id] < 0) return fail(ctx, PT_ERR_INVALID, "table %d has no visit in pass %d", table_id, pass);
     const size_t bytes = (size_t)((ctx->tables[table_id].n + 31) / 32) * 4;
     if (bitmap_out && bytes)
         PT_CUDA(ctx, cudaMemcpyAsync(bitmap_out, ctx->surv[pass][table_id], bytes, cudaMemcpyDefault, ctx->stream));
@@ -1028,6 +1081,7 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     if (pass < 0 || pass > 1 || !out) return fail(ctx, PT_ERR_INVALID, "pass %d / out NULL", pass);
     if (table_id < 0 || table_id >= (int)ctx->tables.size()) return fail(ctx, PT_ERR_INVALID, "table id %d", table_id);
     if (!(ctx->passes_done & (1 << pass))) return fail(ctx, PT_ERR_STATE, "pass %d has not run", pass);
+    if (ctx->vidx[pass][table_id] < 0) return fail(ctx, PT_ERR_INVALID, "table %d has no visit in pass %d", table_id, pass);
     const int T = (int)ctx->tables.size(), E = (int)ctx->edges.size();
     std::vector<unsigned long long> c(T), s(3 * T);
     std::vector<int64_t> nb(std::max(E, 1));
@@ -1035,9 +1089,7 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     PT_CUDA(ctx, cudaMemcpyAsync(s.data(), ctx->stats[pass], 3 * T * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (E) PT_CUDA(ctx, cudaMemcpyAsync(nb.data(), ctx->nblocks[pass], E * 8, cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const Visit* vis = nullptr;
-    for (const Visit& x : ctx->visits[pass])
-        if (x.table == table_id) vis = &x;
+    const Visit* vis = &ctx->visits[pass][ctx->vidx[pass][table_id]];
     std::memset(out, 0, sizeof *out);
     out->n_rows = ctx->tables[table_id].n;
     out->survivors = (int64_t)c[table_id];
@@ -1048,7 +1100,7 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     out->n_in = (int32_t)vis->in_edges.size();
     out->n_out = (int32_t)vis->out_edges.size();
     for (int e : vis->out_edges) out->filter_bytes += nb[e] * ctx->fcfg.block_bits / 8;
-    out->has_input_bitmap = pass == 1 || ctx->tables[table_id].sel != nullptr;
+    out->has_input_bitmap = (pass == 1 && ctx->schedule == PT_SCHEDULE_TRANSFER) || ctx->tables[table_id].sel != nullptr;
     return PT_OK;
 }
 
@@ -1074,6 +1126,16 @@ pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable) {
         ctx->shapes_ready = false;
     }
     ctx->first_probe = enable == 1;
+    return PT_OK;
+}
+
+pt_status pt_set_schedule(pt_ctx* ctx, int32_t schedule) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (schedule != PT_SCHEDULE_TRANSFER && schedule != PT_SCHEDULE_ONE_HOP)
+        return fail(ctx, PT_ERR_INVALID, "schedule must be %d or %d (got %d)", PT_SCHEDULE_TRANSFER,
+                    PT_SCHEDULE_ONE_HOP, schedule);
+    if (ctx->planned) return fail(ctx, PT_ERR_STATE, "the schedule is fixed once planned");
+    ctx->schedule = schedule;
     return PT_OK;
 }
 

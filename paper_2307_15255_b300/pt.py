@@ -104,6 +104,7 @@ _SIGS = {
     "pt_set_first_probe": (C.c_int, [_P, C.c_int32]),
     "pt_set_first_probe_ctas": (C.c_int, [_P, C.c_int32]),
     "pt_set_probe_order": (C.c_int, [_P, C.c_int32]),
+    "pt_set_schedule": (C.c_int, [_P, C.c_int32]),
     "pt_join_count": (C.c_int, [_P, _P]),
     "pt_set_streams": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
@@ -309,6 +310,11 @@ def pt_join_count(ctx: int) -> int:
 
 
 PT_ORDER_LEVEL_LIP, PT_ORDER_LIP, PT_ORDER_EDGE = 0, 1, 2
+PT_SCHEDULE_TRANSFER, PT_SCHEDULE_ONE_HOP = 0, 1
+
+
+def pt_set_schedule(ctx: int, schedule: int) -> None:
+    _check(lib.pt_set_schedule(ctx, int(schedule)), "pt_set_schedule", ctx)
 
 
 def pt_set_probe_order(ctx: int, order: int) -> None:

@@ -31,7 +31,10 @@ class TransferSession:
     a column is a contiguous int32/int64 tensor (CUDA: borrowed; CPU:
     copied to the device, asynchronously when pinned) and ``sel`` an int32
     tensor holding the uint32 selection bitmap words, or ``None``.
-    ``edges``: sequence of ``(t0, (cols of t0), t1, (cols of t1))``.
+    ``edges``: sequence of ``(t0, (cols of t0), t1, (cols of t1))`` or
+    ``(t0, cols, t1, cols, flags)``.  ``schedule``: ``PT_SCHEDULE_TRANSFER``
+    (forward and backward pass) or ``PT_SCHEDULE_ONE_HOP`` (a Bloom join:
+    every filter built from its table's selection, probed once).
     """
 
     def __init__(self, tables: Sequence[Tuple[int, Sequence[torch.Tensor], Optional[torch.Tensor]]],
@@ -39,11 +42,12 @@ class TransferSession:
                  seed: int = 0, stream: Optional[torch.cuda.Stream] = None,
                  launch: Optional[Tuple[int, int, int]] = None, graph: bool = False,
                  cluster: Optional[int] = None, first_probe: Optional[bool] = None,
-                 probe_order: Optional[int] = None):
+                 probe_order: Optional[int] = None, schedule: int = _pt.PT_SCHEDULE_TRANSFER):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.block_bits = block_bits
         self.bits_per_key = bits_per_key
         self.k = k
+        self.schedule = schedule
         self.col_dtypes = []
         self.ctx = _pt.pt_create(bits_per_key, k, block_bits, seed, self.stream.cuda_stream)
         self._keep: List[torch.Tensor] = []
@@ -71,6 +75,7 @@ class TransferSession:
                 _pt.pt_set_first_probe(self.ctx, first_probe)
             if probe_order is not None:
                 _pt.pt_set_probe_order(self.ctx, probe_order)
+            _pt.pt_set_schedule(self.ctx, schedule)
             self.order, self.mem_bytes = _pt.pt_plan(self.ctx, len(self.n_rows))
             if graph:
                 _pt.pt_set_graph_mode(self.ctx, True)
@@ -118,8 +123,14 @@ class TransferSession:
         _pt.pt_get_filter(self.ctx, pass_, edge_id, out.data_ptr())
         return out
 
-    def stats(self, pass_: int, table_id: int) -> dict:
-        return _pt.pt_get_visit_stats(self.ctx, pass_, table_id)
+    def stats(self, pass_: int, table_id: int) -> Optional[dict]:
+        """The visit's accounting; None for a table the pass does not visit."""
+        try:
+            return _pt.pt_get_visit_stats(self.ctx, pass_, table_id)
+        except _pt.PtError as e:
+            if e.status == _pt.PT_ERR_INVALID and self.schedule == _pt.PT_SCHEDULE_ONE_HOP and pass_ == 0:
+                return None
+            raise
 
     def join_count(self) -> int:
         """Size of the join of the survivors (acyclic graphs of inner joins)."""

@@ -26,10 +26,10 @@ def edges_of(w):
 
 
 def session_for(w, launch=None, graph=False, host=False, pin=False, cluster=None, first_probe=None,
-                probe_order=None):
+                probe_order=None, schedule=0):
     return TransferSession(device_tables(w, host, pin), edges_of(w), w.bits_per_key, w.k, w.block_bits,
                            w.seed, launch=launch, graph=graph, cluster=cluster, first_probe=first_probe,
-                           probe_order=probe_order)
+                           probe_order=probe_order, schedule=schedule)
 
 
 def collect(s, w):
@@ -74,3 +74,45 @@ def assert_same(got, want, w, sectors=True):
         for e in range(len(w.edges)):
             assert got["nblocks"][p][e] == want["nblocks"][p][e], (p, e)
             assert np.array_equal(got["filters"][p][e], want["filters"][p][e]), f"pass {p} edge {e}: filters differ"
+
+
+def collect_one_hop(s, w):
+    """A one-hop session's results in the oracle's one_hop() shape: pass 1's
+    survivors, pass 0's filters, and pass 0's survivors of the builders."""
+    out = {"surv": [], "count": [], "filters": [], "nblocks": [], "built": {}}
+    for v in range(w.n_tables):
+        bm, c = s.survivors(v)
+        out["surv"].append(bm.cpu().numpy().view(np.uint32))
+        out["count"].append(c)
+        if s.stats(0, v) is not None:
+            bm0, c0 = s.survivors(v, 0)
+            out["built"][v] = (bm0.cpu().numpy().view(np.uint32), c0)
+    for e in range(len(w.edges)):
+        f = s.filter(0, e).cpu().numpy().view(np.uint32)
+        out["filters"].append(f)
+        out["nblocks"].append(len(f) * 32 // w.block_bits)
+    return out
+
+
+def assert_same_one_hop(got, want, w):
+    for v in range(w.n_tables):
+        n = w.tables[v].n_rows
+        assert np.array_equal(got["surv"][v][: (n + 31) // 32], want["surv"][v]), f"table {v}: survivors differ"
+        assert got["count"][v] == want["count"][v], v
+    for e in range(len(w.edges)):
+        assert got["nblocks"][e] == want["nblocks"][e], e
+        assert np.array_equal(got["filters"][e], want["filters"][e]), f"edge {e}: filters differ"
+    # a builder's pass-0 survivors are its selection
+    for v, (bm, c) in got["built"].items():
+        t = w.tables[v]
+        nw = (t.n_rows + 31) // 32
+        sel = t.sel if t.sel is not None else _all_rows(t.n_rows)
+        assert np.array_equal(bm[:nw], sel[:nw]), v
+        assert c == int(sum(bin(int(x)).count("1") for x in sel[:nw]))
+
+
+def _all_rows(n):
+    words = np.full((n + 31) // 32, 0xFFFFFFFF, np.uint32)
+    if n % 32:
+        words[-1] = (1 << (n % 32)) - 1
+    return words
