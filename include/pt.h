@@ -265,6 +265,18 @@ pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
  * keeps every probe in the scan kernel.  Takes effect at the next run. */
 pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable);
 
+/* Early scans (off by default; only with first-probe passes and
+ * PT_ORDER_LEVEL_LIP).  When a visit with a first-probe pass has incoming
+ * filters from builders below its highest builder level besides the one its
+ * first-probe pass takes, the probes of those filters run as a scan of their
+ * own right after the first-probe pass, while the higher-level builders
+ * still run; the visit's scan then probes the highest level's filters only.
+ * The probe order, survivors, filters and sector accounting are unchanged.
+ * Off by default: on the snowflake benchmark the early scan competes with
+ * the higher-level builders' gathers and the step is slower.  Takes effect
+ * at the next run. */
+pt_status pt_set_early_scan(pt_ctx* ctx, int32_t enable);
+
 /* Order in which a visit probes its incoming filters (Section 3.2,
  * "Transfer Schedule": LIP-style ordering of the incoming filters is an
  * optional optimization).  PT_ORDER_LEVEL_LIP (default): ascending level of

@@ -105,7 +105,12 @@ struct VisitArgs {
     int32_t smem_words;              // shared-memory filter budget of one CTA (uint32 words)
     int32_t total_warps;             // scan warps launched (= segments)
     int32_t cluster;                 // CTAs per thread-block cluster of the scan (1, 2 or 4)
-    int32_t pad_;
+    int32_t level_lo;                // the scan probes only the incoming edges whose build_level is
+    int32_t level_hi;                // >= level_lo and, unless level_hi is 0, < level_hi (an early
+                                     // scan takes the edges whose builders finish first)
+    int32_t insert_sizes;            // 1: no size/clear launch -- the scan (or list probe) zeroes the
+                                     // outgoing filters' words of the previous run (out[].nblocks
+                                     // still holds its sizes) and the insert sizes the filters
     const int32_t* first_in;         // in[] index of the edge a first-probe pass already tested
                                      // (in_bits then holds its survivors), or nullptr
     const uint32_t* list_ids;        // backward list probe: the forward survivors' ids, in segments

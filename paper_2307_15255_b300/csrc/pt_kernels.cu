@@ -301,12 +301,29 @@ struct ScanShared {
     int32_t n_in;            // edges this kernel probes (a first-probe pass may have taken one)
 };
 
+// With a.insert_sizes, zero this visit's outgoing filters as the previous run
+// left them (out[e].nblocks blocks each; the words past them are still zero
+// from the run before, or from the allocation), in 16-byte stores spread over
+// the visit's n_ctas CTAs.  The insert, which follows on the same stream,
+// then sizes the filters and sets their bits.
+__device__ __forceinline__ void clear_previous_filters(const VisitArgs& a, int block_bits, int64_t cta, int64_t n_ctas) {
+    if (!a.insert_sizes) return;
+    const size_t tid = (size_t)cta * blockDim.x + threadIdx.x, stride = (size_t)n_ctas * blockDim.x;
+    for (int e = 0; e < a.n_out; ++e) {
+        uint4* p = reinterpret_cast<uint4*>(a.out[e].filter);
+        const size_t n16 = (size_t)*a.out[e].nblocks * (size_t)(block_bits / 128);
+        for (size_t i = tid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 // Probe order (mode 0, the default): incoming edges by ascending level of the
 // building visit (its longest path from a source of the pass's DAG: filters
 // finished earlier come first), then ascending survivors/rows of the building
 // visit (LIP-style, Section 3.2 "Transfer Schedule"), then edge id.  Mode 1
 // leaves the level out (the LIP ratio, then edge id); mode 2 is edge id alone
-// (unordered).  in[skip] is left out (skip < 0: none).  Writes the in[]
+// (unordered).  in[skip] is left out (skip < 0: none), and so is every edge
+// whose build_level is outside [a.level_lo, a.level_hi) (level_hi 0: no upper
+// bound).  Writes the in[]
 // indexes to ord and returns their number; nbs[i] receives in[i]'s filter
 // size in blocks (every count and size is loaded at once: one round trip).
 // One thread.  In mode 0 the first edge depends only on the counts of the
@@ -319,7 +336,9 @@ __device__ __forceinline__ int lip_order(const VisitArgs& a, int skip, int mode,
     for (int i = 0; i < kMaxIn; ++i) {
         c[i] = i < a.n_in ? *a.in[i].build_count : 0ull;
         nbs[i] = i < a.n_in ? (uint32_t)*a.in[i].nblocks : 0u;
-        if (i < a.n_in && i != skip) ord[m++] = i;
+        const bool in_range = i < a.n_in && a.in[i].build_level >= a.level_lo &&
+                              (a.level_hi == 0 || a.in[i].build_level < a.level_hi);
+        if (in_range && i != skip) ord[m++] = i;
     }
     for (int i = 1; i < m; ++i) {
         const int x = ord[i];
@@ -359,6 +378,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     const uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t sfilt = (uint32_t)__cvta_generic_to_shared(smem);  // shared-window address of the filters
 
+    clear_previous_filters(a, B, cta, a.total_warps / (blockDim.x >> 5));
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
         uint32_t nbs[kMaxIn];
@@ -1096,6 +1116,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
     const uint32_t FULL = 0xFFFFFFFFu;
     constexpr uint32_t kNoRow = 0xFFFFFFFFu;  // rows are below 2^31
 
+    clear_previous_filters(a, B, blockIdx.x, gridDim.x);
     if (threadIdx.x == 0) {
         int ord[kMaxIn];
         uint32_t nbs[kMaxIn];
@@ -1232,6 +1253,13 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
 // ---------------------------------------------------------------------------
 // 2. size + clear the outgoing filters from the device-side survivor count
 // ---------------------------------------------------------------------------
+// The size rule: max(1, ceil(min(c, n_probe) * bits_per_key / block_bits)).
+__device__ __forceinline__ int64_t filter_blocks(unsigned long long c, int64_t n_probe, const FilterCfg& f) {
+    const int64_t n_est = min((int64_t)c, n_probe);
+    const int64_t nb = (n_est * f.bits_per_key + f.block_bits - 1) / f.block_bits;
+    return nb < 1 ? 1 : nb;
+}
+
 // Part `part` of `nparts` of a visit's size/clear (thread t of the part zeroes
 // every (nparts * blockDim)-th 16-byte chunk from (part * blockDim + t)).
 __device__ __forceinline__ void size_clear_part(const VisitArgs& a, const FilterCfg& f, int64_t part, int64_t nparts) {
@@ -1241,9 +1269,7 @@ __device__ __forceinline__ void size_clear_part(const VisitArgs& a, const Filter
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e) {
         if (e >= a.n_out) break;
-        const int64_t n_est = min((int64_t)c, a.out[e].probe_rows);
-        int64_t nb = (n_est * f.bits_per_key + f.block_bits - 1) / f.block_bits;
-        if (nb < 1) nb = 1;
+        const int64_t nb = filter_blocks(c, a.out[e].probe_rows, f);
         if (tid == 0) *a.out[e].nblocks = nb;
         uint4* p = reinterpret_cast<uint4*>(a.out[e].filter);
         const size_t n16 = (size_t)nb * (size_t)(f.block_bits / 128);
@@ -1281,7 +1307,16 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
     using BB = BlockBits<B>;
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e)
-        if (threadIdx.x == (unsigned)e && e < a.n_out) s_nb[e] = (uint32_t)*a.out[e].nblocks;
+        if (threadIdx.x == (unsigned)e && e < a.n_out) {
+            if (a.insert_sizes) {
+                // the scan zeroed the previous run's words; this run's size, from the count
+                const int64_t nb = filter_blocks(*a.count, a.out[e].probe_rows, f);
+                s_nb[e] = (uint32_t)nb;
+                if (part == 0) *a.out[e].nblocks = nb;
+            } else {
+                s_nb[e] = (uint32_t)*a.out[e].nblocks;
+            }
+        }
     __syncthreads();
 
     const uint32_t lane = threadIdx.x & 31;

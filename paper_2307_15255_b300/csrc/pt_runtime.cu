@@ -3,8 +3,8 @@
 // The runtime keeps the registered tables and the join graph, builds the
 // transfer schedule (Section 3.2 of the paper: size-ordered edges, one
 // forward and one backward pass), lays out every buffer a run needs in one
-// device allocation, and enqueues the three kernels of each visit on the
-// context's stream.  No step of a run executes on the host: filter sizes
+// device allocation, and enqueues the kernels of each visit (a first-probe
+// pass where it applies, the scan, the insert) on the context's streams.  No step of a run executes on the host: filter sizes
 // depend on survivor counts that only the device knows, so they are
 // computed by a kernel and no host synchronization happens between visits.
 #include <algorithm>
@@ -66,6 +66,10 @@ struct Visit {
     // (an incoming filter may outgrow the budget); the second one's grid
     bool first_pair = false;
     int first_grid0 = 0;
+    // an early scan (after the first-probe pass, of the other incoming edges whose
+    // builders are below early_level, the highest builder level of the visit)
+    bool early = false;
+    int32_t early_level = 0;
     // a backward visit over the forward survivor list: its launch shape
     bool list = false;
     int list_grid = 0;
@@ -107,7 +111,10 @@ struct pt_ctx {
     unsigned long long* stats[2] = {nullptr, nullptr};   // [table][3]
     int32_t* first_idx = nullptr;                        // [table]: edge the first-probe pass tested
     std::vector<uint32_t*> mid;                          // [table]: its survivors, or nullptr
+    std::vector<uint32_t*> mid2;                         // [table]: the early scan's survivors, or nullptr
+    unsigned long long* early_count[2] = {nullptr, nullptr};  // [table]: the early scan's survivor count
     bool first_probe = true;                             // run first-probe passes where they apply
+    bool early_scan = false;                             // run early scans where they apply
     int first_ctas = 0;                                  // first-probe CTAs per SM (0: as many as fit)
     bool first_pair = true;                              // pairs of first-probe launches (with / without smem)
     int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
@@ -159,6 +166,7 @@ struct pt_ctx {
     // concurrently with the builders of the visit's other filters.
     std::vector<cudaStream_t> fstream;  // per table with a first-probe pass, else nullptr
     std::vector<cudaEvent_t> fev;       // its pass is done
+    std::vector<cudaEvent_t> eev;       // and the early scan after it, where there is one
 };
 
 namespace {
@@ -376,6 +384,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     a.total_warps = sh.total_warps;
     a.smem_words = (int32_t)(sh.filter_smem / 4);
     a.cluster = sh.cluster;
+    a.insert_sizes = 1;
     if (p == 1 && vis.list) {
         const ScanShape& fs = ctx->visits[0][ctx->vidx[0][v]].shape;
         a.words_per_warp = fs.words_per_warp;
@@ -570,10 +579,37 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
             }
             if ((s1 = record_event(ctx, 2, fs, p, v)) != PT_OK) return s1;
             PT_CUDA(ctx, cudaEventRecord(ctx->fev[v], fs));
-            PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->fev[v], 0));
             ctx->launches++;
             a.in_bits = ctx->mid[v];
             a.first_in = ctx->first_idx + v;
+            cudaEvent_t done = ctx->fev[v];
+            if (vis.early && ctx->early_scan && ctx->fcfg.probe_order == 0) {
+                // the other filters of builders below the visit's highest level, in
+                // probe order, as soon as those builders are done: their probes then
+                // overlap the higher-level builders instead of following them
+                if (same_pass)
+                    for (int e : vis.in_edges) {
+                        const int b = ctx->bld[p][e];
+                        if (ctx->lvl[p][b] < vis.early_level) PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][b], 0));
+                    }
+                pt::VisitArgs ea = a;
+                ea.level_hi = vis.early_level;
+                ea.out_bits = ctx->mid2[v];
+                ea.ids = nullptr;
+                ea.seg_count = nullptr;
+                ea.n_out = 0;
+                ea.n_bcols = 0;
+                ea.count = ctx->early_count[p] + v;
+                if ((s1 = record_event(ctx, 0, fs, p, v)) != PT_OK) return s1;
+                PT_CUDA(ctx, pt::launch_scan(ea, ctx->fcfg, sh.grid, sh.block, sh.smem, fs));
+                if ((s1 = record_event(ctx, 0, fs, p, v)) != PT_OK) return s1;
+                PT_CUDA(ctx, cudaEventRecord(ctx->eev[v], fs));
+                ctx->launches++;
+                done = ctx->eev[v];
+                a.in_bits = ctx->mid2[v];
+                a.level_lo = vis.early_level;
+            }
+            PT_CUDA(ctx, cudaStreamWaitEvent(st, done, 0));
         }
         if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
         if (p == 1 && vis.list)
@@ -583,18 +619,15 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
         ctx->launches++;
         if (a.n_out > 0) {
-            int64_t words = 0;
-            for (int e : vis.out_edges) words = std::max(words, ctx->filt_max_words[e]);
-            const int64_t n16 = words / 4;
-            int grid_c = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, (int64_t)ctx->num_sms * 4));
+            // the scan above zeroed the previous run's filter words; the insert sizes
+            // the filters from the survivor count and sets their bits.  256-thread
+            // CTAs (one fits beside two first-probe CTAs), up to six per SM; segments
+            // are split between warps when there are more warps than segments
             if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
-            PT_CUDA(ctx, pt::launch_size_clear(a, ctx->fcfg, grid_c, 512, st));
-            // 256-thread CTAs (one fits beside two first-probe CTAs), up to six per SM;
-            // segments are split between warps when there are more warps than segments
             const int grid_i = std::max(1, std::min(3 * a.total_warps / 8 + 1, ctx->num_sms * 6));
             PT_CUDA(ctx, pt::launch_insert(a, ctx->fcfg, grid_i, 256, st));
             if ((s1 = record_event(ctx, 1, st, p, v)) != PT_OK) return s1;
-            ctx->launches += 2;
+            ctx->launches++;
         }
         PT_CUDA(ctx, cudaEventRecord(ctx->vev[p][v], st));
     }
@@ -677,6 +710,8 @@ pt_status pt_destroy(pt_ctx* ctx) {
     for (cudaStream_t f : ctx->fstream)
         if (f) cudaStreamDestroy(f);
     for (cudaEvent_t e : ctx->fev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->eev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -856,13 +891,27 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             ctx->slot[p][vis.table] = used[l]++;
         }
     }
+    // early scans: a visit with a first-probe pass and, besides the edge that pass
+    // takes (one of the lowest level), more edges from builders below its highest
+    // level
+    for (int p = 0; p < 2; ++p)
+        for (Visit& vis : ctx->visits[p]) {
+            if (!vis.first) continue;
+            int32_t lmax = 0, below = 0;
+            for (int e : vis.in_edges) lmax = std::max(lmax, ctx->lvl[p][ctx->bld[p][e]]);
+            for (int e : vis.in_edges) below += ctx->lvl[p][ctx->bld[p][e]] < lmax;
+            vis.early = below >= 2;
+            vis.early_level = lmax;
+        }
     ctx->fstream.assign(T, nullptr);
     ctx->fev.assign(T, nullptr);
+    ctx->eev.assign(T, nullptr);
     for (int p = 0; p < 2; ++p)
         for (const Visit& vis : ctx->visits[p]) {
             if (!vis.first) continue;
             PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->fstream[vis.table], cudaStreamNonBlocking));
             PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fev[vis.table], cudaEventDisableTiming));
+            if (vis.early) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->eev[vis.table], cudaEventDisableTiming));
         }
 
     // one device allocation holds every buffer of a run
@@ -870,10 +919,13 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     const std::vector<bool>& has_edge = ctx->has_edge;
     size_t off = 0;
     std::vector<size_t> o_surv[2], o_ids[2], o_seg[2], o_filt[2], o_mid(T, 0), o_hash(E, 0);
-    std::vector<bool> has_mid(T, false);
+    std::vector<bool> has_mid(T, false), has_mid2(T, false);
+    std::vector<size_t> o_mid2(T, 0);
     for (int p = 0; p < 2; ++p)
-        for (const Visit& vis : ctx->visits[p])
+        for (const Visit& vis : ctx->visits[p]) {
             if (vis.first) has_mid[vis.table] = true;
+            if (vis.early) has_mid2[vis.table] = true;
+        }
     for (int p = 0; p < 2; ++p) {
         o_surv[p].resize(T);
         o_filt[p].resize(E);
@@ -894,6 +946,8 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         }
         o_mid[v] = off;  // whole 256-row tiles: the first-probe kernel writes 8 words at a time
         if (has_mid[v]) off += align_up((size_t)((n[v] + 255) / 256) * 32);
+        o_mid2[v] = off;
+        if (has_mid2[v]) off += align_up(std::max<size_t>((size_t)((n[v] + 31) / 32) * 4, 16));
     }
     for (int e = 0; e < E; ++e)
         for (int p = 0; p < 2; ++p) {
@@ -905,12 +959,19 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         o_hash[e] = off;
         off += align_up(std::max<size_t>((size_t)n[ctx->src[e]] * 8, 16));
     }
-    // counts [T] u64, stats [T][3] u64, nblocks [E] i64, first-probe edge [T] i32
-    ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 24 + (size_t)std::max(E, 1) * 8 + (size_t)T * 4);
-    size_t o_meta[2];
+    // zeroed at every pass: counts [T] u64, stats [T][3] u64, early-scan counts [T]
+    // u64, first-probe edge [T] i32
+    ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 24 + (size_t)T * 8 + (size_t)T * 4);
+    size_t o_meta[2], o_nblocks[2];
     for (int p = 0; p < 2; ++p) {
         o_meta[p] = off;
         off += ctx->meta_bytes;
+    }
+    // filter sizes [E] i64, kept from run to run: a building visit's scan zeroes the
+    // words its filters had in the previous run
+    for (int p = 0; p < 2; ++p) {
+        o_nblocks[p] = off;
+        off += align_up((size_t)std::max(E, 1) * 8);
     }
     void* arena = nullptr;
     // PT_INJECT_OOM=1 makes this allocation fail on the host (tests of the error path)
@@ -930,12 +991,16 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
         ctx->meta[p] = base + o_meta[p];
         ctx->counts[p] = (unsigned long long*)(base + o_meta[p]);
         ctx->stats[p] = (unsigned long long*)(base + o_meta[p] + (size_t)T * 8);
-        ctx->nblocks[p] = (int64_t*)(base + o_meta[p] + (size_t)T * 32);
+        ctx->early_count[p] = (unsigned long long*)(base + o_meta[p] + (size_t)T * 32);
+        ctx->nblocks[p] = (int64_t*)(base + o_nblocks[p]);
     }
-    ctx->first_idx = (int32_t*)(base + o_meta[0] + (size_t)T * 32 + (size_t)std::max(E, 1) * 8);
+    ctx->first_idx = (int32_t*)(base + o_meta[0] + (size_t)T * 40);
     ctx->mid.assign(T, nullptr);
-    for (int v = 0; v < T; ++v)
+    ctx->mid2.assign(T, nullptr);
+    for (int v = 0; v < T; ++v) {
         if (has_mid[v]) ctx->mid[v] = (uint32_t*)(base + o_mid[v]);
+        if (has_mid2[v]) ctx->mid2[v] = (uint32_t*)(base + o_mid2[v]);
+    }
     for (int p = 0; p < 2; ++p) {
         ctx->ids[p].resize(T);
         ctx->seg[p].resize(T);
@@ -1126,6 +1191,17 @@ pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable) {
         ctx->shapes_ready = false;
     }
     ctx->first_probe = enable == 1;
+    return PT_OK;
+}
+
+pt_status pt_set_early_scan(pt_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, PT_ERR_INVALID, "ctx is NULL");
+    if (enable != 0 && enable != 1) return fail(ctx, PT_ERR_INVALID, "enable must be 0 or 1 (got %d)", enable);
+    if (ctx->early_scan != (enable == 1) && ctx->gexec) {  // the launch sequence changes
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->early_scan = enable == 1;
     return PT_OK;
 }
 

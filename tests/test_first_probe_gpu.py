@@ -144,6 +144,37 @@ def test_first_probe_off_gives_identical_results(oracle_lib):
         s.close()
 
 
+@pytest.mark.parametrize("kw", [
+    dict(int64=True, composite=True, zipf=1.1, bits_per_key=16),
+    dict(int64=False, bits_per_key=10, k=7, block_bits=512),
+])
+def test_early_scan_gives_identical_results(oracle_lib, kw):
+    # the fact table's in-edges come from D2 and D3 (level 0) and M (level 2):
+    # the first-probe pass takes one level-0 filter, the early scan the other,
+    # and the visit's scan M's; the same survivors, filters and sectors as one
+    # scan after M's build
+    import paper_2307_15255_b300.pt as P
+    from _gpu import assert_same, collect, session_for
+    w = W.snowflake(scale=0.25, **kw)
+    want = oracle_lib.transfer(w)
+    with session_for(w, graph=True) as s:
+        P.pt_set_kernel_timing(s.ctx, True)
+        for flag in (True, False, True):
+            P.pt_set_early_scan(s.ctx, flag)
+            s.run()
+            got = collect(s, w)
+            assert_same(got, want, w)
+            kt = P.pt_get_kernel_times(s.ctx)
+            assert kt["scan_launches"] == 2 * w.n_tables + int(flag)
+    # no early scan in the other probe orders (their order may interleave levels)
+    with session_for(w, probe_order=1) as s:
+        P.pt_set_early_scan(s.ctx, True)
+        P.pt_set_kernel_timing(s.ctx, True)
+        s.run()
+        assert_same(collect(s, w), oracle_lib.transfer(w, probe_order=1), w)
+        assert P.pt_get_kernel_times(s.ctx)["scan_launches"] == 2 * w.n_tables
+
+
 def _two_tables(n_fact, seed, dtype=np.int64):
     """A fact table of n_fact rows whose one key joins a 5000-row dim with a 3% selection."""
     rng = np.random.default_rng(seed)
@@ -180,7 +211,7 @@ def test_kernel_times_split_probe_phase():
             s.run()
         kt = P.pt_get_kernel_times(s.ctx)
         assert kt["first_launches"] == 1  # the fact table's forward visit only
-        assert kt["scan_launches"] == 2 * w.n_tables
+        assert kt["scan_launches"] == 2 * w.n_tables  # one per visit (no early scan by default)
         assert kt["first_ms"] > 0 and kt["scan_ms"] > 0 and kt["build_ms"] > 0
         tot = P.pt_get_kernel_time(s.ctx)
         assert tot["scan_launches"] == kt["first_launches"] + kt["scan_launches"]
