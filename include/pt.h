@@ -265,6 +265,14 @@ pt_status pt_set_cluster(pt_ctx* ctx, int32_t max_cluster);
  * keeps every probe in the scan kernel.  Takes effect at the next run. */
 pt_status pt_set_first_probe(pt_ctx* ctx, int32_t enable);
 
+/* Programmatic dependent launches (on by default): a visit's scan (or list
+ * probe) and insert are launched so that each may start while the kernel
+ * before it on its stream ends; every such kernel first waits on the device
+ * for that kernel's results (griddepcontrol.wait).  Results are the same
+ * either way.  Not used in runs timed by pt_set_kernel_timing.  Takes effect
+ * at the next run. */
+pt_status pt_set_dependent_launch(pt_ctx* ctx, int32_t enable);
+
 /* Early scans (off by default; only with first-probe passes and
  * PT_ORDER_LEVEL_LIP).  When a visit with a first-probe pass has incoming
  * filters from builders below its highest builder level besides the one its

@@ -145,16 +145,21 @@ cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t*
                                int32_t smem_words, int32_t gate_words, int32_t gate, int grid, int block,
                                size_t smem, cudaStream_t s);
 int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem);
+// pdl: launch with programmatic stream serialization (the kernel may start
+// while the previous kernel on the stream runs; it waits for that kernel's
+// results with griddepcontrol.wait before touching memory).
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
-                        cudaStream_t s);
+                        cudaStream_t s, bool pdl = false);
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
-cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s,
+                          bool pdl = false);
 // launch_probe_list: a backward visit over the forward survivors listed at
 // a.list_ids / a.list_seg, probing with the stored hashes in[].hin; writes
 // a.out_bits (every word of the table), a.ids / a.seg_count (same segment
 // geometry), a.count and a.stats.  grid * block / 32 warps walk the
 // a.total_warps segments.
-cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s,
+                              bool pdl = false);
 cudaError_t probe_list_set_smem_limit(int block_bits, size_t smem);
 
 // Batched launches read their task range {first, count} from device memory

@@ -127,6 +127,15 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     return r;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel on its stream still
+// runs.  grid_dependency_wait() returns once that kernel has completed and its
+// memory operations are visible (at once for a kernel launched without the
+// attribute); allow_dependents() lets the next such kernel on the stream
+// launch once every CTA of this one has called it or exited.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <int B>
 struct BlockBits {
     static constexpr uint32_t LOGB = B == 256 ? 8 : 9;
@@ -827,6 +836,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         }
     }
 
+    allow_dependents();  // the next kernel on the stream may launch; it waits for this grid's end
     local = __reduce_add_sync(FULL, local);
     psec = __reduce_add_sync(FULL, (unsigned)psec);
     bsec = __reduce_add_sync(FULL, (unsigned)bsec);
@@ -844,6 +854,7 @@ template <int B, int KT>
 __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks) pt_scan_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ScanShared sh;
+    grid_dependency_wait();
     scan_cta<B, KT, true>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
 }
 
@@ -854,6 +865,7 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanSparseMinBlocks)
     pt_scan_sparse_kernel(const VisitArgs a, const FilterCfg f) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ScanShared sh;
+    grid_dependency_wait();
     scan_cta<B, KT, false>(a, f, blockIdx.x, a.cluster > 1 ? cluster_rank() : 0u, smem, sh);
 }
 
@@ -1111,6 +1123,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ ScanShared sh;
     __shared__ uint32_t s_last[kListThreads / 32][kMaxIn + 1];  // per warp: last row of each stage; [kMaxIn]: survivors
+    grid_dependency_wait();
     constexpr uint32_t WPB = B / 32;
     constexpr int R = kListRows;
     const uint32_t FULL = 0xFFFFFFFFu;
@@ -1241,6 +1254,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
         if (lane == 0 && a.seg_count) a.seg_count[seg] = ocnt;
         total += ocnt;
     }
+    allow_dependents();  // the next kernel on the stream may launch; it waits for this grid's end
     psec = __reduce_add_sync(FULL, (unsigned)psec);
     bsec = __reduce_add_sync(FULL, (unsigned)bsec);
     if (lane == 0) {
@@ -1398,7 +1412,9 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
 template <int B, int KT>
 __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
     __shared__ uint32_t s_nb[kMaxOut];
+    grid_dependency_wait();
     insert_part<B, KT>(a, f, blockIdx.x, gridDim.x, s_nb);
+    allow_dependents();
 }
 
 template <int B, int KT>
@@ -1422,9 +1438,9 @@ __global__ void __launch_bounds__(512)
 
 namespace {
 template <typename K, typename... Args>
-cudaError_t launch_maybe_cluster(K kernel, int cluster, int grid, int block, size_t smem, cudaStream_t s,
-                                 Args... args) {
-    if (cluster <= 1) {
+cudaError_t launch_ex(K kernel, int cluster, bool pdl, int grid, int block, size_t smem, cudaStream_t s,
+                      Args... args) {
+    if (cluster <= 1 && !pdl) {
         kernel<<<grid, block, smem, s>>>(args...);
         return cudaGetLastError();
     }
@@ -1433,34 +1449,43 @@ cudaError_t launch_maybe_cluster(K kernel, int cluster, int grid, int block, siz
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute at[2];
+    unsigned n = 0;
+    if (cluster > 1) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = cluster;
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (pdl) {
+        at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = n;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 }  // namespace
 
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool pdl) {
     const int c = a.cluster;
     if (a.in_bits) {
         if (f.block_bits == 512) {
-            if (f.k == 4) return launch_maybe_cluster(pt_scan_sparse_kernel<512, 4>, c, grid, block, smem, s, a, f);
-            return launch_maybe_cluster(pt_scan_sparse_kernel<512, 0>, c, grid, block, smem, s, a, f);
+            if (f.k == 4) return launch_ex(pt_scan_sparse_kernel<512, 4>, c, pdl, grid, block, smem, s, a, f);
+            return launch_ex(pt_scan_sparse_kernel<512, 0>, c, pdl, grid, block, smem, s, a, f);
         }
-        if (f.k == 4) return launch_maybe_cluster(pt_scan_sparse_kernel<256, 4>, c, grid, block, smem, s, a, f);
-        return launch_maybe_cluster(pt_scan_sparse_kernel<256, 0>, c, grid, block, smem, s, a, f);
+        if (f.k == 4) return launch_ex(pt_scan_sparse_kernel<256, 4>, c, pdl, grid, block, smem, s, a, f);
+        return launch_ex(pt_scan_sparse_kernel<256, 0>, c, pdl, grid, block, smem, s, a, f);
     }
     if (f.block_bits == 512) {
-        if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<512, 4>, c, grid, block, smem, s, a, f);
-        return launch_maybe_cluster(pt_scan_kernel<512, 0>, c, grid, block, smem, s, a, f);
+        if (f.k == 4) return launch_ex(pt_scan_kernel<512, 4>, c, pdl, grid, block, smem, s, a, f);
+        return launch_ex(pt_scan_kernel<512, 0>, c, pdl, grid, block, smem, s, a, f);
     }
-    if (f.k == 4) return launch_maybe_cluster(pt_scan_kernel<256, 4>, c, grid, block, smem, s, a, f);
-    return launch_maybe_cluster(pt_scan_kernel<256, 0>, c, grid, block, smem, s, a, f);
+    if (f.k == 4) return launch_ex(pt_scan_kernel<256, 4>, c, pdl, grid, block, smem, s, a, f);
+    return launch_ex(pt_scan_kernel<256, 0>, c, pdl, grid, block, smem, s, a, f);
 }
 
 cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t* mid, int32_t* first,
@@ -1493,27 +1518,24 @@ cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s) {
+cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s, bool pdl) {
     if (f.block_bits == 512) {
-        if (f.k == 4) pt_insert_kernel<512, 4><<<grid, block, 0, s>>>(a, f);
-        else pt_insert_kernel<512, 0><<<grid, block, 0, s>>>(a, f);
-    } else {
-        if (f.k == 4) pt_insert_kernel<256, 4><<<grid, block, 0, s>>>(a, f);
-        else pt_insert_kernel<256, 0><<<grid, block, 0, s>>>(a, f);
+        if (f.k == 4) return launch_ex(pt_insert_kernel<512, 4>, 1, pdl, grid, block, 0, s, a, f);
+        return launch_ex(pt_insert_kernel<512, 0>, 1, pdl, grid, block, 0, s, a, f);
     }
-    return cudaGetLastError();
+    if (f.k == 4) return launch_ex(pt_insert_kernel<256, 4>, 1, pdl, grid, block, 0, s, a, f);
+    return launch_ex(pt_insert_kernel<256, 0>, 1, pdl, grid, block, 0, s, a, f);
 }
 
-cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_probe_list(const VisitArgs& a, const FilterCfg& f, int grid, size_t smem, cudaStream_t s,
+                              bool pdl) {
     const int block = kListThreads;
     if (f.block_bits == 512) {
-        if (f.k == 4) pt_probe_list_kernel<512, 4><<<grid, block, smem, s>>>(a, f);
-        else pt_probe_list_kernel<512, 0><<<grid, block, smem, s>>>(a, f);
-    } else {
-        if (f.k == 4) pt_probe_list_kernel<256, 4><<<grid, block, smem, s>>>(a, f);
-        else pt_probe_list_kernel<256, 0><<<grid, block, smem, s>>>(a, f);
+        if (f.k == 4) return launch_ex(pt_probe_list_kernel<512, 4>, 1, pdl, grid, block, smem, s, a, f);
+        return launch_ex(pt_probe_list_kernel<512, 0>, 1, pdl, grid, block, smem, s, a, f);
     }
-    return cudaGetLastError();
+    if (f.k == 4) return launch_ex(pt_probe_list_kernel<256, 4>, 1, pdl, grid, block, smem, s, a, f);
+    return launch_ex(pt_probe_list_kernel<256, 0>, 1, pdl, grid, block, smem, s, a, f);
 }
 
 cudaError_t probe_list_set_smem_limit(int block_bits, size_t smem) {
@@ -1568,11 +1590,11 @@ cudaError_t scan_set_smem_limit(int block_bits, size_t smem) {
 cudaError_t launch_scan_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
                               const FilterCfg& f, int cluster, int grid, int block, size_t smem, cudaStream_t s) {
     if (f.block_bits == 512) {
-        if (f.k == 4) return launch_maybe_cluster(pt_scan_batch_kernel<512, 4>, cluster, grid, block, smem, s, visits, tasks, range, f);
-        return launch_maybe_cluster(pt_scan_batch_kernel<512, 0>, cluster, grid, block, smem, s, visits, tasks, range, f);
+        if (f.k == 4) return launch_ex(pt_scan_batch_kernel<512, 4>, cluster, false, grid, block, smem, s, visits, tasks, range, f);
+        return launch_ex(pt_scan_batch_kernel<512, 0>, cluster, false, grid, block, smem, s, visits, tasks, range, f);
     }
-    if (f.k == 4) return launch_maybe_cluster(pt_scan_batch_kernel<256, 4>, cluster, grid, block, smem, s, visits, tasks, range, f);
-    return launch_maybe_cluster(pt_scan_batch_kernel<256, 0>, cluster, grid, block, smem, s, visits, tasks, range, f);
+    if (f.k == 4) return launch_ex(pt_scan_batch_kernel<256, 4>, cluster, false, grid, block, smem, s, visits, tasks, range, f);
+    return launch_ex(pt_scan_batch_kernel<256, 0>, cluster, false, grid, block, smem, s, visits, tasks, range, f);
 }
 
 cudaError_t launch_size_clear_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,

@@ -106,6 +106,7 @@ _SIGS = {
     "pt_set_probe_order": (C.c_int, [_P, C.c_int32]),
     "pt_set_schedule": (C.c_int, [_P, C.c_int32]),
     "pt_set_early_scan": (C.c_int, [_P, C.c_int32]),
+    "pt_set_dependent_launch": (C.c_int, [_P, C.c_int32]),
     "pt_join_count": (C.c_int, [_P, _P]),
     "pt_set_streams": (C.c_int, [_P, C.c_int32]),
     "pt_get_kernel_times": (C.c_int, [_P, C.POINTER(pt_kernel_times)]),
@@ -316,6 +317,10 @@ PT_SCHEDULE_TRANSFER, PT_SCHEDULE_ONE_HOP = 0, 1
 
 def pt_set_early_scan(ctx: int, enable: bool) -> None:
     _check(lib.pt_set_early_scan(ctx, 1 if enable else 0), "pt_set_early_scan", ctx)
+
+
+def pt_set_dependent_launch(ctx: int, enable: bool) -> None:
+    _check(lib.pt_set_dependent_launch(ctx, 1 if enable else 0), "pt_set_dependent_launch", ctx)
 
 
 def pt_set_schedule(ctx: int, schedule: int) -> None:
