@@ -33,10 +33,35 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 __device__ __forceinline__ uint64_t hash_key(uint64_t x, uint64_t seed) { return mix64((x ^ seed) + kGamma); }
 
+// Loads of data a kernel reads once (key columns, bitmaps, row lists): through
+// the read-only path without allocating in L1, which is left to the filters
+// probed through it.  Volatile, so that none moves above a kernel's
+// griddepcontrol.wait.
+__device__ __forceinline__ int32_t ld_once(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_once(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ long long ld_once(const long long* p) {
+    long long v;
+    asm volatile("ld.global.nc.L1::no_allocate.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_once(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L1::no_allocate.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
 // Key of row r as u64; int32 values are sign-extended.
 __device__ __forceinline__ uint64_t load_key(const ColRef& c, uint32_t r) {
-    if (c.dtype == 0) return (uint64_t)(int64_t)__ldg(reinterpret_cast<const int32_t*>(c.p) + r);
-    return (uint64_t)__ldg(reinterpret_cast<const long long*>(c.p) + r);
+    if (c.dtype == 0) return (uint64_t)(int64_t)ld_once(reinterpret_cast<const int32_t*>(c.p) + r);
+    return (uint64_t)ld_once(reinterpret_cast<const long long*>(c.p) + r);
 }
 
 // Hash of row r's key on an edge.  A first column of dtype kHashed already
@@ -600,7 +625,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     auto load_word = [&](int64_t w) -> uint32_t {
         uint32_t x = 0;
         if (w < w_end) {
-            x = a.in_bits ? __ldg(a.in_bits + w) : FULL;
+            x = a.in_bits ? ld_once(a.in_bits + w) : FULL;
             if (w == n_words - 1 && tail_bits) x &= (1u << tail_bits) - 1u;
         }
         return x;
@@ -617,11 +642,11 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         if (d_col.dtype == 0) {
             const int32_t* p = reinterpret_cast<const int32_t*>(d_col.p) + row0 + lane;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)(int64_t)__ldg(p + 32 * i);
+            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)(int64_t)ld_once(p + 32 * i);
         } else {
             const long long* p = reinterpret_cast<const long long*>(d_col.p) + row0 + lane;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)__ldg(p + 32 * i);
+            for (int i = 0; i < 8; ++i) kv[i] = (uint64_t)ld_once(p + 32 * i);
         }
     };
     uint64_t kn[8];  // prefetched keys (valid when have_pref)
@@ -1006,10 +1031,10 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
             const int64_t r0 = t * kFirstTileRows + lane;
             if (t < n_full) {
 #pragma unroll
-                for (int i = 0; i < R; ++i) kv[i] = (uint64_t)__ldg(col + r0 + 32 * i);
+                for (int i = 0; i < R; ++i) kv[i] = (uint64_t)ld_once(col + r0 + 32 * i);
             } else {
 #pragma unroll
-                for (int i = 0; i < R; ++i) kv[i] = r0 + 32 * i < n ? (uint64_t)__ldg(col + r0 + 32 * i) : 0ull;
+                for (int i = 0; i < R; ++i) kv[i] = r0 + 32 * i < n ? (uint64_t)ld_once(col + r0 + 32 * i) : 0ull;
             }
         };
         uint64_t kv[R];
@@ -1187,7 +1212,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
             for (int i = 0; i < R; ++i) {
                 const uint32_t idx = b + lane + 32u * i;
                 live[i] = idx < cnt;
-                r[i] = live[i] ? __ldg(ids + idx) : kNoRow;
+                r[i] = live[i] ? ld_once(ids + idx) : kNoRow;
             }
             for (int s = 0; s < n_in; ++s) {
                 const ProbeEdge& pe = sh.pe[s];
@@ -1195,7 +1220,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
                 if (pe.hin) {  // the hashes the forward insert stored
                     const unsigned long long* hin = reinterpret_cast<const unsigned long long*>(pe.hin) + slot0;
 #pragma unroll
-                    for (int i = 0; i < R; ++i) h[i] = live[i] ? __ldg(hin + b + lane + 32u * i) : 0ull;
+                    for (int i = 0; i < R; ++i) h[i] = live[i] ? ld_once(hin + b + lane + 32u * i) : 0ull;
                 } else {       // an edge the forward pass did not build on (one-way): gather and hash
 #pragma unroll
                     for (int i = 0; i < R; ++i) h[i] = live[i] ? edge_hash(pe.col[0], pe.col[1], pe.ncols, r[i], f.seed) : 0ull;
@@ -1355,7 +1380,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
             for (int i = 0; i < 4; ++i) {
                 const uint32_t idx = base + lane + 32u * i;
                 live[i] = idx < cnt;
-                r[i] = live[i] ? ids[idx] : 0u;
+                r[i] = live[i] ? ld_once(ids + idx) : 0u;
             }
 #pragma unroll
             for (int e = 0; e < kMaxOut; ++e) {
