@@ -1374,18 +1374,20 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
         const uint32_t* ids = a.ids + (size_t)s * seg_rows;
         // four survivors per lane at a time: four independent key gathers in flight
         for (uint32_t base = 128u * (uint32_t)(t / a.total_warps); base < cnt; base += 128u * (uint32_t)ways) {
-            uint32_t r[4];
+            uint32_t r[4], live_mask[4];
             bool live[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const uint32_t idx = base + lane + 32u * i;
                 live[i] = idx < cnt;
+                live_mask[i] = __ballot_sync(0xFFFFFFFFu, live[i]);
                 r[i] = live[i] ? ld_once(ids + idx) : 0u;
             }
 #pragma unroll
             for (int e = 0; e < kMaxOut; ++e) {
                 if (e >= a.n_out) break;
                 const BuildEdge& be = a.out[e];
+                const bool dedup = a.n > be.probe_rows;
                 uint64_t h[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(be.col[0], be.col[1], be.ncols, r[i], seed) : 0ull;
@@ -1399,6 +1401,15 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (!live[i]) continue;
+                    // lanes holding the same hash set the same bits: only the lowest one
+                    // does.  Keys repeat when the building table has more rows than the
+                    // other end (foreign keys, skewed ones piling atomics on a few words);
+                    // the smaller side's keys are mostly distinct, and the match would
+                    // only cost time
+                    if (dedup) {
+                        const uint32_t peers = __match_any_sync(live_mask[i], h[i]);
+                        if (lane != (uint32_t)(__ffs(peers) - 1)) continue;
+                    }
                     const uint32_t lo = (uint32_t)h[i];
                     uint32_t* blk = be.filter + (size_t)mul_hi((uint32_t)(h[i] >> 32), s_nb[e]) * BB::WPB;
                     const uint32_t h2 = (lo >> 16) | 1u;
