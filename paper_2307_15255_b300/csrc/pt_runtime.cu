@@ -160,7 +160,7 @@ struct pt_ctx {
     cudaStream_t aux[kAux] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> vev[2];  // per pass, per table: the visit's work is done
     cudaEvent_t pass_ev[2] = {nullptr, nullptr};
-    std::vector<int> slot[2];         // per pass, per table: position inside its level
+    std::vector<int> slot[2];         // per pass, per table: its stream (index into aux)
     std::vector<int32_t> lvl[2];      // per pass, per table: level (longest path from a source)
     // A first-probe pass runs on a stream of its own, as soon as the filters
     // of its visit's lowest-level builders exist (it probes one of those),
@@ -878,16 +878,14 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     if (!one_hop)
         for (Visit& vis : ctx->visits[1]) vis.list = ctx->has_edge[vis.table];
 
-    // streams and events for concurrent visits; slot = position of a visit
-    // among the visits of its level (level = longest path from a source of
-    // that pass's DAG)
+    // streams and events for concurrent visits (level = longest path from a
+    // source of the pass's DAG)
     for (int i = 0; i < pt_ctx::kAux; ++i)
         if (!ctx->aux[i]) PT_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
     for (int p = 0; p < 2; ++p) {
         if (!ctx->pass_ev[p]) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pass_ev[p], cudaEventDisableTiming));
         ctx->vev[p].assign(T, nullptr);
         for (int v = 0; v < T; ++v) PT_CUDA(ctx, cudaEventCreateWithFlags(&ctx->vev[p][v], cudaEventDisableTiming));
-        std::vector<int> used;
         std::vector<int32_t>& lvl = ctx->lvl[p];
         lvl.assign(T, 0);
         for (const Visit& vis : ctx->visits[p])
@@ -895,11 +893,39 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                 const int to = ctx->prb[p][e];
                 if (to >= 0) lvl[to] = std::max(lvl[to], lvl[vis.table] + 1);
             }
+        // streams (slot = index into aux): within a level, bigger tables choose
+        // first, and a visit takes the stream of its biggest builder in this pass
+        // unless another visit of the level has it; else the first stream the level
+        // leaves free.  The chain of big visits, which is the critical path, then
+        // stays on one stream: its kernels follow one another with no cross-stream
+        // wait and launch as programmatic dependents
         ctx->slot[p].assign(T, 0);
-        for (const Visit& vis : ctx->visits[p]) {
-            const int l = lvl[vis.table];
-            if ((int)used.size() <= l) used.resize(l + 1, 0);
-            ctx->slot[p][vis.table] = used[l]++;
+        int max_l = 0;
+        for (const Visit& vis : ctx->visits[p]) max_l = std::max(max_l, lvl[vis.table]);
+        for (int l = 0; l <= max_l; ++l) {
+            std::vector<int> vs;
+            for (const Visit& vis : ctx->visits[p])
+                if (lvl[vis.table] == l) vs.push_back(vis.table);
+            std::stable_sort(vs.begin(), vs.end(), [&](int x, int y) { return n[x] > n[y]; });
+            bool taken[pt_ctx::kAux] = {};
+            int wrap = 0;
+            for (int v : vs) {
+                int pref = -1;
+                int64_t biggest = -1;
+                for (int e : ctx->visits[p][ctx->vidx[p][v]].in_edges) {
+                    const int b = ctx->bld[p][e];
+                    if (b >= 0 && ctx->vidx[p][b] >= 0 && n[b] > biggest) {
+                        biggest = n[b];
+                        pref = ctx->slot[p][b];
+                    }
+                }
+                int sl = pref >= 0 && !taken[pref] ? pref : -1;
+                for (int i = 0; sl < 0 && i < pt_ctx::kAux; ++i)
+                    if (!taken[i]) sl = i;
+                if (sl < 0) sl = wrap++ % pt_ctx::kAux;  // more visits in the level than streams
+                taken[sl] = true;
+                ctx->slot[p][v] = sl;
+            }
         }
     }
     // early scans: a visit with a first-probe pass and, besides the edge that pass
