@@ -65,7 +65,7 @@ def _time_graph(session, warmup: int, runs: int) -> float:
     return e0.elapsed_time(e1) / runs
 
 
-def tune(session, candidates: Optional[Iterable[Tuple[int, int, int]]] = None, warmup: int = 2, runs: int = 5,
+def tune(session, candidates: Optional[Iterable[Tuple[int, int, int]]] = None, warmup: int = 3, runs: int = 20,
          cache_path: Optional[str] = None, use_cache: bool = True) -> Dict[str, object]:
     """Pick the fastest launch shape for ``session`` and leave it applied.
 
