@@ -1247,6 +1247,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const uint32_t m = __ballot_sync(FULL, live[i]);
+                if (m == 0) continue;  // (warp-uniform) no survivor in this group of 32: nothing to write
                 if (a.ids && live[i]) a.ids[slot0 + ocnt + __popc(m & lt_mask)] = r[i];
                 ocnt += __popc(m);
                 // word runs: rows ascend across lanes, so equal words are adjacent
