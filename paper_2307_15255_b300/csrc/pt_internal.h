@@ -145,6 +145,23 @@ cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t*
                                int32_t smem_words, int32_t gate_words, int32_t gate, int grid, int block,
                                size_t smem, cudaStream_t s);
 int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem);
+// Parts a batched first probe of a visit of n rows is split into (host and
+// device agree on it): about kFirstTilesPerPart tiles each.
+constexpr int64_t kFirstTilesPerPart = 1024;
+__host__ __device__ inline int64_t first_parts(int64_t n) {
+    const int64_t tiles = (n + kFirstTileRows - 1) / kFirstTileRows;
+    const int64_t p = (tiles + kFirstTilesPerPart - 1) / kFirstTilesPerPart;
+    return p < 1 ? 1 : p;
+}
+// launch_probe_first_batch: the first probes of a batch's visits (task t is
+// part tasks[t].part of visit tasks[t].visit); a visit's in_bits receives the
+// rows that pass and first_in the in[] index of the edge it took.  The filter
+// goes to shared memory when it fits smem_words; gate and gate_words as for
+// launch_probe_first, per task.
+cudaError_t launch_probe_first_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                                     const FilterCfg& f, int32_t smem_words, int32_t gate_words, int32_t gate,
+                                     int grid, size_t smem, cudaStream_t s);
+int probe_first_batch_max_ctas_per_sm(int block_bits, size_t smem);
 // pdl: launch with programmatic stream serialization (the kernel may start
 // while the previous kernel on the stream runs; it waits for that kernel's
 // results with griddepcontrol.wait before touching memory).

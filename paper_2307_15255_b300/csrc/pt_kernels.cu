@@ -951,14 +951,24 @@ __global__ void __launch_bounds__(kScanMaxThreads, kScanMinBlocks)
 // survivor words are 8 ballots.  The keys of the warp's next tile are
 // loaded before the current tile is hashed.
 // ---------------------------------------------------------------------------
+struct FirstShared {
+    ProbeEdge pe;
+    uint32_t nb;
+    int32_t fit, run;
+};
+
+// CTA `cta` of the n_ctas a visit's first probe is split into (every thread of
+// the block calls it; it returns at once when the gate says the other launch of
+// a pair has the filter).
 template <int B, int KT>
-__global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
-    pt_probe_first_kernel(const VisitArgs a, const FilterCfg f, uint32_t* __restrict__ mid, int32_t* first,
-                          const int32_t smem_words, const int32_t gate_words, const int32_t gate) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ ProbeEdge s_pe;
-    __shared__ uint32_t s_nb;
-    __shared__ int32_t s_fit, s_run;
+__device__ __forceinline__ void probe_first_cta(const VisitArgs& a, const FilterCfg& f, uint32_t* __restrict__ mid,
+                                                int32_t* first, const int32_t smem_words, const int32_t gate_words,
+                                                const int32_t gate, const int64_t cta, const int64_t n_ctas,
+                                                uint32_t* smem, FirstShared& fs) {
+    ProbeEdge& s_pe = fs.pe;
+    uint32_t& s_nb = fs.nb;
+    int32_t& s_fit = fs.fit;
+    int32_t& s_run = fs.run;
     constexpr uint32_t WPB = B / 32;
     constexpr int R = kFirstTileRows / 32;  // rows per lane of a tile
     const uint32_t FULL = 0xFFFFFFFFu;
@@ -972,7 +982,7 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
         // gate 1: run only if the filter fits gate_words; 2: only if it does not
         const bool fits = (int64_t)s_nb * WPB <= (int64_t)gate_words;
         s_run = gate == 0 || (gate == 1) == fits;
-        if (blockIdx.x == 0 && s_run) *first = ord[0];
+        if (cta == 0 && s_run) *first = ord[0];
     }
     __syncthreads();
     if (!s_run) return;  // the other launch of the pair has this filter
@@ -990,8 +1000,8 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
     const int64_t n_words = (n + 31) >> 5;
     const int64_t n_tiles = (n + kFirstTileRows - 1) / kFirstTileRows;
     const int64_t n_full = n / kFirstTileRows;  // tiles with every row inside the table
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t W = n_ctas * (blockDim.x >> 5);
+    const int64_t gw = cta * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const ColRef c0 = s_pe.col[0], c1 = s_pe.col[1];
     const int ncols = s_pe.ncols;
     const uint32_t* fg = s_pe.filter;
@@ -1083,7 +1093,7 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
 
     // key sectors this stage read: every sector of the edge's column(s)
     unsigned long long psec = 0;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t w = cta * blockDim.x + threadIdx.x; w < n_words; w += n_ctas * blockDim.x) {
         const uint32_t tail = (uint32_t)(n & 31);
         const uint32_t alive = (w == n_words - 1 && tail) ? (1u << tail) - 1u : FULL;
         psec += sectors_of(alive, c0.dtype);
@@ -1094,6 +1104,39 @@ __global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
     if (lane == 0 && psec) {
         atomicAdd(a.stats + 0, psec);
         atomicAdd(a.stats + 2, psec);
+    }
+}
+
+template <int B, int KT>
+__global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
+    pt_probe_first_kernel(const VisitArgs a, const FilterCfg f, uint32_t* __restrict__ mid, int32_t* first,
+                          const int32_t smem_words, const int32_t gate_words, const int32_t gate) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ FirstShared fs;
+    probe_first_cta<B, KT>(a, f, mid, first, smem_words, gate_words, gate, blockIdx.x, gridDim.x, smem, fs);
+}
+
+// Batched first probes: task t is part tasks[t].part of the first_parts(n)
+// parts of visit tasks[t].visit's first probe.  The visit's in_bits is the
+// bitmap the probe writes and first_in the slot of the edge it takes (the
+// visit's scan then reads them as its input); its rows all start alive.
+template <int B, int KT>
+__global__ void __launch_bounds__(kFirstThreads, kFirstMinBlocks)
+    pt_probe_first_batch_kernel(const VisitArgs* visits, const BatchTask* task_base, const int32_t* range,
+                                const FilterCfg f, const int32_t smem_words, const int32_t gate_words,
+                                const int32_t gate) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ FirstShared fs;
+    __shared__ __align__(16) VisitArgs s_a;
+    const BatchTask* tasks = task_base + range[0];
+    const int32_t n = range[1];
+    for (int32_t t = blockIdx.x; t < n; t += gridDim.x) {
+        const BatchTask task = tasks[t];
+        load_visit(s_a, visits + task.visit);
+        __syncthreads();
+        probe_first_cta<B, KT>(s_a, f, const_cast<uint32_t*>(s_a.in_bits), const_cast<int32_t*>(s_a.first_in),
+                               smem_words, gate_words, gate, task.part, first_parts(s_a.n), smem, fs);
+        __syncthreads();
     }
 }
 
@@ -1536,6 +1579,36 @@ cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t*
         else pt_probe_first_kernel<256, 0><<<grid, block, smem, s>>>(a, f, mid, first, smem_words, gate_words, gate);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_probe_first_batch(const VisitArgs* visits, const BatchTask* tasks, const int32_t* range,
+                                     const FilterCfg& f, int32_t smem_words, int32_t gate_words, int32_t gate,
+                                     int grid, size_t smem, cudaStream_t s) {
+    const int block = kFirstThreads;
+    if (f.block_bits == 512) {
+        if (f.k == 4)
+            pt_probe_first_batch_kernel<512, 4><<<grid, block, smem, s>>>(visits, tasks, range, f, smem_words, gate_words, gate);
+        else
+            pt_probe_first_batch_kernel<512, 0><<<grid, block, smem, s>>>(visits, tasks, range, f, smem_words, gate_words, gate);
+    } else {
+        if (f.k == 4)
+            pt_probe_first_batch_kernel<256, 4><<<grid, block, smem, s>>>(visits, tasks, range, f, smem_words, gate_words, gate);
+        else
+            pt_probe_first_batch_kernel<256, 0><<<grid, block, smem, s>>>(visits, tasks, range, f, smem_words, gate_words, gate);
+    }
+    return cudaGetLastError();
+}
+
+int probe_first_batch_max_ctas_per_sm(int block_bits, size_t smem) {
+    int n = 0, m = 0;
+    if (block_bits == 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_probe_first_batch_kernel<512, 4>, kFirstThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_probe_first_batch_kernel<512, 0>, kFirstThreads, smem);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_probe_first_batch_kernel<256, 4>, kFirstThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_probe_first_batch_kernel<256, 0>, kFirstThreads, smem);
+    }
+    return n < m ? n : m;
 }
 
 int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem) {

@@ -55,8 +55,9 @@ constexpr int kFilterSmem = 16 * 1024;   // shared-memory filter budget of a bat
                                          // 1318 batched queries per second)
 constexpr int kCluster = 1;              // batched scan CTAs per cluster (1: no cluster-spread filters)
 constexpr size_t kAl = 256;
-constexpr int kLaunchesPerLevel = 3;     // scan, size/clear, insert
-constexpr int kMetaWordsPerPass = kMaxInst * 3 + kMaxQEdges;  // count, 2 sector counters per instance; nblocks per edge
+constexpr int kLaunchesPerLevel = 4;     // first probe, scan, size/clear, insert
+constexpr int kMetaWordsPerPass = kMaxInst * 4 + kMaxQEdges;  // count, 3 sector counters per instance; nblocks per edge
+constexpr int kFirstSmem = 40 * 1024;    // filter budget of a batched first-probe CTA (three per SM)
 
 size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 double now_s() {
@@ -118,6 +119,7 @@ class Arena {
 struct QVisit {
     int inst = 0;
     int level = 0;
+    bool first = false;  // a first-probe pass (forward, every row alive, a large table)
     std::vector<int> in_edges, out_edges;
     std::vector<int> bcols;
     int64_t grid = 1;  // scan tasks (CTAs)
@@ -141,6 +143,7 @@ struct Query {
     // device layout (offsets inside the query's arena allocation)
     size_t bytes = 0, base = 0;
     size_t o_surv[2][kMaxInst] = {}, o_ids[kMaxInst] = {}, o_seg[kMaxInst] = {}, o_sel[kMaxInst] = {};
+    size_t o_mid[kMaxInst] = {}, o_first[kMaxInst] = {};  // a first-probe pass's bitmap and edge slot
     size_t o_filt[2][kMaxQEdges] = {};
     int64_t filt_words[kMaxQEdges] = {};
     // state
@@ -181,7 +184,7 @@ struct pt_server {
 
     DescLayout dl;
     Slot slots[kMaxSlots];
-    int scan_grid = 1, clear_grid = 1, insert_grid = 1;
+    int scan_grid = 1, clear_grid = 1, insert_grid = 1, first_grid = 1, first_grid0 = 1;
     size_t scan_smem = 0;
     cudaStream_t copy_stream = nullptr;
 
@@ -271,6 +274,10 @@ pt_status plan_query(pt_server* S, Query* q) {
             }
             lvl[vis.inst] = vis.level;
             q->lvl[p][vis.inst] = vis.level;
+            // every row of a large instance without a selection starts alive: its first
+            // probe streams the edge's hash column in a launch of its own
+            vis.first = p == 0 && !vis.in_edges.empty() && q->sel[vis.inst].empty() && !q->sel_dev[vis.inst] &&
+                        n[vis.inst] >= pt::kFirstMinRows;
             // scan tasks: tiles of kTileWords words, each run by a cluster of kCluster CTAs
             const int64_t words = (n[vis.inst] + 31) / 32;
             vis.grid = std::max<int64_t>(1, (words + kTileWords - 1) / kTileWords);
@@ -294,6 +301,13 @@ pt_status plan_query(pt_server* S, Query* q) {
         }
         q->o_sel[v] = off;
         if (!q->sel[v].empty()) off += wb;
+        bool first = false;
+        for (const QVisit& vis : q->visits[0])
+            if (vis.inst == v) first = vis.first;
+        q->o_mid[v] = off;  // whole 256-row tiles: the first probe writes 8 words at a time
+        if (first) off += al((size_t)((n[v] + 255) / 256) * 32);
+        q->o_first[v] = off;
+        if (first) off += al(16);
         q->o_ids[v] = off;
         if (has_edge[v]) off += al(std::max<size_t>((size_t)n[v] * 4, 16));
         q->o_seg[v] = off;
@@ -336,15 +350,19 @@ void fill_args(pt_server* S, const Query* q, int p, const QVisit& vis, unsigned 
     unsigned char* base = S->arena + q->base;
     unsigned long long* counts = meta_dev + p * kMetaWordsPerPass;
     unsigned long long* stats = counts + kMaxInst;
-    int64_t* nblocks = (int64_t*)(counts + 3 * kMaxInst);
+    int64_t* nblocks = (int64_t*)(counts + 4 * kMaxInst);
     a.n = S->tables[q->table[v]].n;
     if (p == 0)
         a.in_bits = q->sel_dev[v] ? q->sel_dev[v] : q->sel[v].empty() ? nullptr : (const uint32_t*)(base + q->o_sel[v]);
     else
         a.in_bits = (const uint32_t*)(base + q->o_surv[0][v]);
+    if (vis.first) {  // the first-probe pass writes these, the scan reads them
+        a.in_bits = (const uint32_t*)(base + q->o_mid[v]);
+        a.first_in = (const int32_t*)(base + q->o_first[v]);
+    }
     a.out_bits = (uint32_t*)(base + q->o_surv[p][v]);
     a.count = counts + v;
-    a.stats = stats + 2 * v;
+    a.stats = stats + 3 * v;
     a.n_in = (int)vis.in_edges.size();
     a.n_out = (int)vis.out_edges.size();
     a.words_per_warp = vis.wpw;
@@ -401,11 +419,21 @@ pt_status enqueue_batch_launches(pt_server* S, Slot& sl, int lf, int lb) {
     for (int p = 0; p < 2; ++p) {
         const int L = p == 0 ? lf : lb;
         for (int l = 0; l < L; ++l) {
-            SRV_CUDA(pt::launch_scan_batch(visits, tasks, ranges + 2 * launch_index(p, l, 0), S->fcfg, kCluster,
+            if (p == 0) {
+                // a pair over the same tasks: filters that fit the budget are probed from
+                // shared memory, the others with all of L1 (each launch returns at once
+                // from the other's tasks)
+                const int32_t* rf = ranges + 2 * launch_index(p, l, 0);
+                SRV_CUDA(pt::launch_probe_first_batch(visits, tasks, rf, S->fcfg, kFirstSmem / 4, kFirstSmem / 4, 1,
+                                                      S->first_grid, kFirstSmem, sl.stream));
+                SRV_CUDA(pt::launch_probe_first_batch(visits, tasks, rf, S->fcfg, 0, kFirstSmem / 4, 2,
+                                                      S->first_grid0, 0, sl.stream));
+            }
+            SRV_CUDA(pt::launch_scan_batch(visits, tasks, ranges + 2 * launch_index(p, l, 1), S->fcfg, kCluster,
                                            S->scan_grid, kScanWarps * 32, S->scan_smem, sl.stream));
-            SRV_CUDA(pt::launch_size_clear_batch(visits, tasks, ranges + 2 * launch_index(p, l, 1), kClearParts,
+            SRV_CUDA(pt::launch_size_clear_batch(visits, tasks, ranges + 2 * launch_index(p, l, 2), kClearParts,
                                                  S->fcfg, S->clear_grid, 512, sl.stream));
-            SRV_CUDA(pt::launch_insert_batch(visits, tasks, ranges + 2 * launch_index(p, l, 2), kInsertParts, S->fcfg,
+            SRV_CUDA(pt::launch_insert_batch(visits, tasks, ranges + 2 * launch_index(p, l, 3), kInsertParts, S->fcfg,
                                              S->insert_grid, 512, sl.stream));
         }
     }
@@ -469,9 +497,28 @@ pt_status launch_batch(pt_server* S, Slot& sl) {
     for (int p = 0; p < 2; ++p) {
         const int Lp = p == 0 ? lf : lb;
         for (int l = 0; l < Lp; ++l) {
+            // first probes, part-major across queries: queries whose first probe
+            // streams the same hash column read its rows at about the same time
+            int32_t* rf = ranges + 2 * launch_index(p, l, 0);
+            rf[0] = nt;
+            int64_t pmax = 0;
+            for (int i = 0; i < nq; ++i)
+                for (const QVisit& vis : sl.batch[i]->visits[p])
+                    if (vis.level == l && vis.first)
+                        pmax = std::max(pmax, pt::first_parts(S->tables[sl.batch[i]->table[vis.inst]].n));
+            for (int64_t g = 0; g < pmax; ++g)
+                for (int i = 0; i < nq; ++i)
+                    for (size_t j = 0; j < sl.batch[i]->visits[p].size(); ++j) {
+                        const QVisit& vis = sl.batch[i]->visits[p][j];
+                        if (vis.level != l || !vis.first) continue;
+                        if (g >= pt::first_parts(S->tables[sl.batch[i]->table[vis.inst]].n)) continue;
+                        if (nt >= L.max_tasks) return fail(PT_ERR_INVALID, "batch exceeds %d tasks", L.max_tasks);
+                        tasks[nt++] = pt::BatchTask{vidx[p][i][j], (int32_t)g};
+                    }
+            rf[1] = nt - rf[0];
             // scans: tile-major across queries, so the queries' tasks on the same
             // rows of a shared table run close together (their column reads hit L2)
-            int32_t* r = ranges + 2 * launch_index(p, l, 0);
+            int32_t* r = ranges + 2 * launch_index(p, l, 1);
             r[0] = nt;
             int64_t gmax = 0;
             for (int i = 0; i < nq; ++i)
@@ -486,8 +533,8 @@ pt_status launch_batch(pt_server* S, Slot& sl) {
                         tasks[nt++] = pt::BatchTask{vidx[p][i][j], (int32_t)g};
                     }
             r[1] = nt - r[0];
-            for (int kind = 1; kind <= 2; ++kind) {
-                const int parts = kind == 1 ? kClearParts : kInsertParts;
+            for (int kind = 2; kind <= 3; ++kind) {
+                const int parts = kind == 2 ? kClearParts : kInsertParts;
                 int32_t* rr = ranges + 2 * launch_index(p, l, kind);
                 rr[0] = nt;
                 for (int part = 0; part < parts; ++part)
@@ -683,7 +730,9 @@ pt_status pt_server_start(pt_server* S) {
     int64_t max_grid = 1;
     for (const ResTable& t : S->tables)
         max_grid = std::max<int64_t>(max_grid, ((t.n + 31) / 32 + kTileWords - 1) / kTileWords);
-    const int64_t mt = (int64_t)S->max_batch * 2 * kMaxInst * (max_grid + kClearParts + kInsertParts);
+    int64_t max_first = 1;
+    for (const ResTable& t : S->tables) max_first = std::max<int64_t>(max_first, pt::first_parts(t.n));
+    const int64_t mt = (int64_t)S->max_batch * 2 * kMaxInst * (max_grid + max_first + kClearParts + kInsertParts);
     L.max_tasks = (int)std::min<int64_t>(mt, 1 << 24);
     L.o_visits = 0;
     L.o_ranges = al((size_t)L.max_visits * sizeof(pt::VisitArgs));
@@ -714,6 +763,8 @@ pt_status pt_server_start(pt_server* S) {
     S->scan_grid = S->num_sms * fit / kCluster * kCluster;
     S->clear_grid = S->num_sms * 2;
     S->insert_grid = S->num_sms * 2;
+    S->first_grid = S->num_sms * std::max(1, pt::probe_first_batch_max_ctas_per_sm(S->fcfg.block_bits, kFirstSmem));
+    S->first_grid0 = S->num_sms * std::max(1, pt::probe_first_batch_max_ctas_per_sm(S->fcfg.block_bits, 0));
     S->started = true;
     S->worker = std::thread(worker_loop, S);
     return PT_OK;
