@@ -57,7 +57,7 @@ typedef enum {
     PT_ERR_CUDA = 3,        /* a CUDA call failed (message in pt_last_error) */
     PT_ERR_STATE = 4,       /* call out of order (e.g. run before pt_plan) */
     PT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
-    PT_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    PT_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } pt_status;
 
 typedef enum { PT_I32 = 0, PT_I64 = 1 } pt_dtype;

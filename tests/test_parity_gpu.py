@@ -391,3 +391,19 @@ def test_join_count_star_forest_and_one_way(oracle_lib):
         with pytest.raises(P.PtError) as ei:
             s.join_count()
         assert ei.value.status == P.PT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("pdl,streams,graph", [(False, 3, False), (False, 1, True), (True, 1, False), (True, 3, True)])
+def test_dependent_launches_and_streams(oracle_lib, pdl, streams, graph):
+    # programmatic dependent launches on or off, every visit on one stream or
+    # spread over three, direct launches or a captured graph: the same results
+    from _gpu import assert_same, collect, session_for
+    from paper_2307_15255_b300 import pt as P
+    w = W.snowflake(scale=0.25, int64=True, composite=True, zipf=1.1, bits_per_key=16)
+    want = oracle_lib.transfer(w)
+    with session_for(w, graph=graph) as s:
+        P.pt_set_dependent_launch(s.ctx, pdl)
+        P.pt_set_streams(s.ctx, streams)
+        for _ in range(2):
+            s.run()
+        assert_same(collect(s, w), want, w)
