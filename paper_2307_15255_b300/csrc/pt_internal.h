@@ -168,6 +168,10 @@ int probe_first_batch_max_ctas_per_sm(int block_bits, size_t smem);
 cudaError_t launch_scan(const VisitArgs& a, const FilterCfg& f, int grid, int block, size_t smem,
                         cudaStream_t s, bool pdl = false);
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s);
+// launch_pass_through: for a backward visit that probes nothing (its survivors
+// are its forward ones), zero its filters' words of the previous run and add
+// its build columns' sectors (from a.out_bits) to a.stats[1].
+cudaError_t launch_pass_through(const VisitArgs& a, const FilterCfg& f, int grid, cudaStream_t s, bool pdl);
 cudaError_t launch_insert(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s,
                           bool pdl = false);
 // launch_probe_list: a backward visit over the forward survivors listed at

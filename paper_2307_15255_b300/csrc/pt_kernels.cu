@@ -1489,6 +1489,39 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
     }
 }
 
+// A backward visit that probes nothing (a source of the reversed DAG) keeps
+// its forward survivors, so no scan runs for it: this kernel does the two
+// things such a scan would have done for its builds -- zero its filters' words
+// of the previous run, and count the build columns' sectors holding a
+// survivor, from the survivor words.
+__global__ void __launch_bounds__(512) pt_pass_through_kernel(const VisitArgs a, const FilterCfg f) {
+    grid_dependency_wait();
+    clear_previous_filters(a, f.block_bits, blockIdx.x, gridDim.x);
+    // the survivor words in 16-byte loads, four of them in flight per thread (the
+    // bitmap's allocation is 16-byte aligned; words past the table are zero)
+    const int64_t n_words = (a.n + 31) >> 5, n16 = (n_words + 3) >> 2;
+    const uint4* w4 = reinterpret_cast<const uint4*>(a.out_bits);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long bsec = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = i + u * stride < n16 ? __ldcs(w4 + i + u * stride) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t w0 = (i + u * stride) * 4;
+            const uint32_t m[4] = {v[u].x, w0 + 1 < n_words ? v[u].y : 0u, w0 + 2 < n_words ? v[u].z : 0u,
+                                   w0 + 3 < n_words ? v[u].w : 0u};
+            for (int c = 0; c < a.n_bcols; ++c)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bsec += sectors_of(m[j], a.bcol[c].dtype);
+        }
+    }
+    allow_dependents();
+    bsec = __reduce_add_sync(0xFFFFFFFFu, (unsigned)bsec);
+    if ((threadIdx.x & 31) == 0 && bsec) atomicAdd(a.stats + 1, bsec);
+}
+
 template <int B, int KT>
 __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
     __shared__ uint32_t s_nb[kMaxOut];
@@ -1621,6 +1654,10 @@ int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_probe_first_kernel<256, 0>, block, smem);
     }
     return n < m ? n : m;
+}
+
+cudaError_t launch_pass_through(const VisitArgs& a, const FilterCfg& f, int grid, cudaStream_t s, bool pdl) {
+    return launch_ex(pt_pass_through_kernel, 1, pdl, grid, 512, 0, s, a, f);
 }
 
 cudaError_t launch_size_clear(const VisitArgs& a, const FilterCfg& f, int grid, int block, cudaStream_t s) {

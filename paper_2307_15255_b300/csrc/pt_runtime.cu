@@ -72,6 +72,10 @@ struct Visit {
     int32_t early_level = 0;
     // a backward visit over the forward survivor list: its launch shape
     bool list = false;
+    // a backward visit that probes nothing (a source of the reversed DAG): its
+    // survivors, row ids and segment counts are its forward ones (aliased), no
+    // scan runs, and its builds read the forward count
+    bool pass_through = false;
     int list_grid = 0;
     size_t list_smem = 0;
 };
@@ -363,6 +367,13 @@ ScanShape scan_shape(pt_ctx* ctx, const Visit& vis, bool sparse) {
     return s;
 }
 
+// Survivor count of table v after pass p on the device (a pass-through
+// backward visit's is its forward one).
+unsigned long long* count_of(pt_ctx* ctx, int p, int v) {
+    const bool through = p == 1 && ctx->vidx[1][v] >= 0 && ctx->visits[1][ctx->vidx[1][v]].pass_through;
+    return ctx->counts[through ? 0 : p] + v;
+}
+
 pt::ColRef colref(const pt_ctx* ctx, int t, int c) {
     pt::ColRef r{};
     r.p = ctx->tables[t].cols[c].dev;
@@ -383,7 +394,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     const bool one_hop = ctx->schedule == PT_SCHEDULE_ONE_HOP;
     a.in_bits = p == 0 || one_hop ? ctx->tables[v].sel : ctx->surv[0][v];
     a.out_bits = ctx->surv[p][v];
-    a.count = ctx->counts[p] + v;
+    a.count = count_of(ctx, p, v);
     a.stats = ctx->stats[p] + 3 * v;
     a.n_in = (int)vis.in_edges.size();
     a.n_out = (int)vis.out_edges.size();
@@ -414,7 +425,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         pe.col[1] = ed.ncols == 2 ? colref(ctx, v, cs[1]) : pe.col[0];
         pe.filter = ctx->filt[fp][e];
         pe.nblocks = ctx->nblocks[fp] + e;
-        pe.build_count = ctx->counts[fp] + b;
+        pe.build_count = count_of(ctx, fp, b);
         pe.build_rows = ctx->tables[b].n;
         pe.build_level = ctx->lvl[fp][b];
         // stored by the forward insert, unless this one-way edge built nothing forward
@@ -623,7 +634,9 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         // records of a timed run
         const bool pdl = ctx->pdl && !ctx->timing;
         if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
-        if (p == 1 && vis.list)
+        if (vis.pass_through)
+            PT_CUDA(ctx, pt::launch_pass_through(a, ctx->fcfg, ctx->num_sms * 2, st, pdl));
+        else if (p == 1 && vis.list)
             PT_CUDA(ctx, pt::launch_probe_list(a, ctx->fcfg, vis.list_grid, vis.list_smem, st, pdl));
         else
             PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st, pdl));
@@ -876,7 +889,10 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     }
     // a backward visit of a table with an edge starts from its forward survivor list
     if (!one_hop)
-        for (Visit& vis : ctx->visits[1]) vis.list = ctx->has_edge[vis.table];
+        for (Visit& vis : ctx->visits[1]) {
+            vis.list = ctx->has_edge[vis.table];
+            vis.pass_through = vis.list && vis.in_edges.empty() && !vis.out_edges.empty();
+        }
 
     // streams and events for concurrent visits (level = longest path from a
     // source of the pass's DAG)
@@ -1048,6 +1064,12 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     }
     ctx->hfwd.resize(E);
     for (int e = 0; e < E; ++e) ctx->hfwd[e] = (uint64_t*)(base + o_hash[e]);
+    for (const Visit& vis : ctx->visits[1])
+        if (vis.pass_through) {
+            ctx->surv[1][vis.table] = ctx->surv[0][vis.table];
+            ctx->ids[1][vis.table] = ctx->ids[0][vis.table];
+            ctx->seg[1][vis.table] = ctx->seg[0][vis.table];
+        }
     // bitmaps of tables nobody visits with data still read as zero tails
     PT_CUDA(ctx, cudaMemsetAsync(arena, 0, off, ctx->stream));
     ctx->planned = true;
@@ -1148,7 +1170,7 @@ pt_status pt_get_pass_survivors(pt_ctx* ctx, int32_t pass, int32_t table_id, uin
         PT_CUDA(ctx, cudaMemcpyAsync(bitmap_out, ctx->surv[pass][table_id], bytes, cudaMemcpyDefault, ctx->stream));
     unsigned long long c = 0;
     if (count_out)
-        PT_CUDA(ctx, cudaMemcpyAsync(&c, ctx->counts[pass] + table_id, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+        PT_CUDA(ctx, cudaMemcpyAsync(&c, count_of(ctx, pass, table_id), sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (count_out) *count_out = (int64_t)c;
     return PT_OK;
@@ -1195,6 +1217,11 @@ pt_status pt_get_visit_stats(pt_ctx* ctx, int32_t pass, int32_t table_id, pt_vis
     std::memset(out, 0, sizeof *out);
     out->n_rows = ctx->tables[table_id].n;
     out->survivors = (int64_t)c[table_id];
+    if (vis->pass_through) {  // its count is its forward one
+        unsigned long long cf = 0;
+        PT_CUDA(ctx, cudaMemcpy(&cf, count_of(ctx, pass, table_id), sizeof cf, cudaMemcpyDeviceToHost));
+        out->survivors = (int64_t)cf;
+    }
     out->probe_sectors = (int64_t)s[3 * table_id];
     out->build_sectors = (int64_t)s[3 * table_id + 1];
     out->first_probe_sectors = (int64_t)s[3 * table_id + 2];
@@ -1479,7 +1506,8 @@ pt_status pt_join_count(pt_ctx* ctx, uint64_t* count_out) {
     }
     // survivor counts size each child's hash table (at most half full)
     std::vector<unsigned long long> cnt(T);
-    PT_CUDA(ctx, cudaMemcpyAsync(cnt.data(), ctx->counts[p], T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    for (int v = 0; v < T; ++v)
+        PT_CUDA(ctx, cudaMemcpyAsync(&cnt[v], count_of(ctx, p, v), 8, cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     uint64_t cap = 1024;
     for (int v = 0; v < T; ++v)
