@@ -1393,7 +1393,9 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
         if (threadIdx.x == (unsigned)e && e < a.n_out) {
             if (a.insert_sizes) {
                 // the scan zeroed the previous run's words; this run's size, from the count
-                const int64_t nb = filter_blocks(*a.count, a.out[e].probe_rows, f);
+                // (the size rule with the block size known here: a shift, not a division)
+                const int64_t n_est = min((int64_t)*a.count, a.out[e].probe_rows);
+                const int64_t nb = max((int64_t)1, (n_est * f.bits_per_key + B - 1) / B);
                 s_nb[e] = (uint32_t)nb;
                 if (part == 0) *a.out[e].nblocks = nb;
             } else {
