@@ -11,7 +11,8 @@ constexpr int kMaxIn = 8;         // incoming edges of one visit
 constexpr int kMaxOut = 8;        // outgoing edges of one visit
 constexpr int kMaxBuildCols = 8;  // distinct build columns of one visit
 constexpr int kRoundWords = 128;  // bitmap words (32 rows each) a scan warp takes per round
-constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words
+constexpr int kChunkWords = 32;   // granularity of a scan warp's chunk of words (dense input)
+constexpr int kSparseChunkWords = 8;  // the same for an input bitmap (no dense sub-rounds to keep whole)
 constexpr int kDrain = 128;       // a probe stage runs once its queue holds this many rows
 constexpr int kQueueCap = kDrain + 256;  // row-id queue in front of a probe stage (per warp): room for
                                          // a drain's worth plus 8 dense words (256 rows) or a sparse sub-round

@@ -57,7 +57,6 @@ __device__ __forceinline__ unsigned long long ld_once(const unsigned long long* 
     asm volatile("ld.global.nc.L1::no_allocate.b64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
-
 // Key of row r as u64; int32 values are sign-extended.
 __device__ __forceinline__ uint64_t load_key(const ColRef& c, uint32_t r) {
     if (c.dtype == 0) return (uint64_t)(int64_t)ld_once(reinterpret_cast<const int32_t*>(c.p) + r);
@@ -333,7 +332,23 @@ struct ScanShared {
     uint32_t nb[kMaxIn];
     uint32_t split[kMaxIn];  // 1: the filter is spread over the cluster (this CTA holds its part)
     int32_t n_in;            // edges this kernel probes (a first-probe pass may have taken one)
+    unsigned long long sum[3];  // the CTA's survivors and key sectors (see warp_to_cta)
 };
+
+// Counters that every warp of a grid adds to (a visit's survivor count and its
+// sector accounting) are summed per CTA in shared memory first, and one thread
+// of the CTA adds the sums to the global counters: atomics on one address are
+// serialised at one L2 slice, about 2 ns apiece on B300 (measured: three
+// counters added by each of 3552 warps took 7.9 us, by each of 444 CTAs 1.9 us).
+// Lane 0 of each warp calls warp_to_cta; after a __syncthreads, thread 0 calls
+// cta_to_global, which also clears the CTA's sum for the block's next task.
+__device__ __forceinline__ void warp_to_cta(unsigned long long* s, unsigned long long v) {
+    if (v) atomicAdd(s, v);
+}
+__device__ __forceinline__ void cta_to_global(unsigned long long* s, unsigned long long* g) {
+    if (*s) atomicAdd(g, *s);
+    *s = 0;
+}
 
 // With a.insert_sizes, zero this visit's outgoing filters as the previous run
 // left them (out[e].nblocks blocks each; the words past them are still zero
@@ -418,6 +433,7 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
         uint32_t nbs[kMaxIn];
         const int m = lip_order(a, a.first_in ? *a.first_in : -1, f.probe_order, ord, nbs);
         sh.n_in = m;
+        sh.sum[0] = sh.sum[1] = sh.sum[2] = 0;
         // Shared-memory placement, greedily in probe order: a whole copy in
         // every CTA when it fits, else (in a cluster) 1/C of it in each CTA of
         // the cluster, else probed from global memory.  Every CTA of a cluster
@@ -867,9 +883,15 @@ __device__ __forceinline__ void scan_cta(const VisitArgs& a, const FilterCfg& f,
     bsec = __reduce_add_sync(FULL, (unsigned)bsec);
     if (lane == 0) {
         if (a.seg_count && gw < a.total_warps) a.seg_count[gw] = local;
-        if (local) atomicAdd(a.count, (unsigned long long)local);
-        if (psec) atomicAdd(a.stats + 0, psec);
-        if (bsec) atomicAdd(a.stats + 1, bsec);
+        warp_to_cta(&sh.sum[0], local);
+        warp_to_cta(&sh.sum[1], psec);
+        warp_to_cta(&sh.sum[2], bsec);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cta_to_global(&sh.sum[0], a.count);
+        cta_to_global(&sh.sum[1], a.stats + 0);
+        cta_to_global(&sh.sum[2], a.stats + 1);
     }
     // no CTA of a cluster leaves (or reuses its shared memory) while another may still read its part
     if (C > 1) cooperative_groups::this_cluster().sync();
@@ -955,6 +977,7 @@ struct FirstShared {
     ProbeEdge pe;
     uint32_t nb;
     int32_t fit, run;
+    unsigned long long sum;  // the CTA's key sectors (see warp_to_cta)
 };
 
 // CTA `cta` of the n_ctas a visit's first probe is split into (every thread of
@@ -983,6 +1006,7 @@ __device__ __forceinline__ void probe_first_cta(const VisitArgs& a, const Filter
         const bool fits = (int64_t)s_nb * WPB <= (int64_t)gate_words;
         s_run = gate == 0 || (gate == 1) == fits;
         if (cta == 0 && s_run) *first = ord[0];
+        fs.sum = 0;
     }
     __syncthreads();
     if (!s_run) return;  // the other launch of the pair has this filter
@@ -1101,9 +1125,12 @@ __device__ __forceinline__ void probe_first_cta(const VisitArgs& a, const Filter
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) psec += __shfl_xor_sync(FULL, psec, o);
-    if (lane == 0 && psec) {
-        atomicAdd(a.stats + 0, psec);
-        atomicAdd(a.stats + 2, psec);
+    if (lane == 0) warp_to_cta(&fs.sum, psec);
+    __syncthreads();
+    if (threadIdx.x == 0 && fs.sum) {
+        atomicAdd(a.stats + 0, fs.sum);
+        atomicAdd(a.stats + 2, fs.sum);
+        fs.sum = 0;
     }
 }
 
@@ -1203,6 +1230,7 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
         uint32_t nbs[kMaxIn];
         const int m = lip_order(a, -1, f.probe_order, ord, nbs);
         sh.n_in = m;
+        sh.sum[0] = sh.sum[1] = sh.sum[2] = 0;
         int32_t used = 0;
         for (int i = 0; i < m; ++i) {
             sh.pe[i] = a.in[ord[i]];
@@ -1327,9 +1355,15 @@ __global__ void __launch_bounds__(kListThreads, kListMinBlocks)
     psec = __reduce_add_sync(FULL, (unsigned)psec);
     bsec = __reduce_add_sync(FULL, (unsigned)bsec);
     if (lane == 0) {
-        if (total) atomicAdd(a.count, (unsigned long long)total);
-        if (psec) atomicAdd(a.stats + 0, psec);
-        if (bsec) atomicAdd(a.stats + 1, bsec);
+        warp_to_cta(&sh.sum[0], total);
+        warp_to_cta(&sh.sum[1], psec);
+        warp_to_cta(&sh.sum[2], bsec);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cta_to_global(&sh.sum[0], a.count);
+        cta_to_global(&sh.sum[1], a.stats + 0);
+        cta_to_global(&sh.sum[2], a.stats + 1);
     }
 }
 
@@ -1497,6 +1531,9 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
 // of the previous run, and count the build columns' sectors holding a
 // survivor, from the survivor words.
 __global__ void __launch_bounds__(512) pt_pass_through_kernel(const VisitArgs a, const FilterCfg f) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
     grid_dependency_wait();
     clear_previous_filters(a, f.block_bits, blockIdx.x, gridDim.x);
     // the survivor words in 16-byte loads, four of them in flight per thread (the
@@ -1521,7 +1558,9 @@ __global__ void __launch_bounds__(512) pt_pass_through_kernel(const VisitArgs a,
     }
     allow_dependents();
     bsec = __reduce_add_sync(0xFFFFFFFFu, (unsigned)bsec);
-    if ((threadIdx.x & 31) == 0 && bsec) atomicAdd(a.stats + 1, bsec);
+    if ((threadIdx.x & 31) == 0) warp_to_cta(&s_sum, bsec);
+    __syncthreads();
+    if (threadIdx.x == 0) cta_to_global(&s_sum, a.stats + 1);
 }
 
 template <int B, int KT>

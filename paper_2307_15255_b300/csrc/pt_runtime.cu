@@ -354,15 +354,18 @@ ScanShape scan_shape(pt_ctx* ctx, const Visit& vis, bool sparse) {
     if (ctx->ctas_per_sm > 0) fit = std::min(fit, ctx->ctas_per_sm);
     int64_t max_grid = (int64_t)ctx->num_sms * fit;
     max_grid = std::max<int64_t>(s.cluster, max_grid / s.cluster * s.cluster);
-    const int64_t want_warps = (n_words + pt::kChunkWords - 1) / pt::kChunkWords;  // at least a chunk each
+    // at least a chunk each; a visit with an input bitmap takes no dense 32-word
+    // sub-rounds, so its warps may take fewer words (more warps for a small table)
+    const int64_t chunk = sparse ? pt::kSparseChunkWords : pt::kChunkWords;
+    const int64_t want_warps = (n_words + chunk - 1) / chunk;
     int64_t grid = (want_warps + warps_per_cta - 1) / warps_per_cta;
     grid = (grid + s.cluster - 1) / s.cluster * s.cluster;
     grid = std::max<int64_t>(s.cluster, std::min(grid, max_grid));
     s.grid = (int)grid;
     s.total_warps = (int)(grid * warps_per_cta);
     int64_t wpw = (n_words + s.total_warps - 1) / s.total_warps;
-    wpw = (wpw + pt::kChunkWords - 1) / pt::kChunkWords * pt::kChunkWords;
-    if (wpw < pt::kChunkWords) wpw = pt::kChunkWords;
+    wpw = (wpw + chunk - 1) / chunk * chunk;
+    if (wpw < chunk) wpw = chunk;
     s.words_per_warp = (int)wpw;
     return s;
 }
