@@ -112,6 +112,11 @@ struct VisitArgs {
     int32_t insert_sizes;            // 1: no size/clear launch -- the scan (or list probe) zeroes the
                                      // outgoing filters' words of the previous run (out[].nblocks
                                      // still holds its sizes) and the insert sizes the filters
+    int32_t n_clear_extra;           // out[n_out .. n_out + n_clear_extra): filters of the table's
+                                     // next-pass visit (only filter and nblocks set) whose words of
+                                     // the previous run this visit's scan zeroes as well
+    int32_t insert_bsec;             // 1: the insert counts the build columns' sectors holding a
+                                     // survivor into stats[1] (no scan ran for the visit)
     const int32_t* first_in;         // in[] index of the edge a first-probe pass already tested
                                      // (in_bits then holds its survivors), or nullptr
     const uint32_t* list_ids;        // backward list probe: the forward survivors' ids, in segments

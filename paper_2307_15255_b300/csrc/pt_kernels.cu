@@ -354,11 +354,13 @@ __device__ __forceinline__ void cta_to_global(unsigned long long* s, unsigned lo
 // left them (out[e].nblocks blocks each; the words past them are still zero
 // from the run before, or from the allocation), in 16-byte stores spread over
 // the visit's n_ctas CTAs.  The insert, which follows on the same stream,
-// then sizes the filters and sets their bits.
+// then sizes the filters and sets their bits.  a.n_clear_extra more entries
+// of out[] are filters the table's next-pass visit builds, when that visit
+// runs no scan of its own (its insert follows later in the same run).
 __device__ __forceinline__ void clear_previous_filters(const VisitArgs& a, int block_bits, int64_t cta, int64_t n_ctas) {
     if (!a.insert_sizes) return;
     const size_t tid = (size_t)cta * blockDim.x + threadIdx.x, stride = (size_t)n_ctas * blockDim.x;
-    for (int e = 0; e < a.n_out; ++e) {
+    for (int e = 0; e < a.n_out + a.n_clear_extra; ++e) {
         uint4* p = reinterpret_cast<uint4*>(a.out[e].filter);
         const size_t n16 = (size_t)*a.out[e].nblocks * (size_t)(block_bits / 128);
         for (size_t i = tid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -1416,12 +1418,19 @@ __global__ void __launch_bounds__(512)
 // ---------------------------------------------------------------------------
 // 3. insert the survivors' outgoing keys
 // ---------------------------------------------------------------------------
+struct InsertShared {
+    uint32_t nb[kMaxOut];    // this run's filter sizes
+    unsigned long long sum;  // the CTA's build sectors (with a.insert_bsec; see warp_to_cta)
+};
+
 // Part `part` of `nparts` of a visit's insert: warp w of the part takes the
 // segments s = part * warps + w, then every (nparts * warps)-th one.
 template <int B, int KT>
 __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg& f, int64_t part, int64_t nparts,
-                                            uint32_t* s_nb) {
+                                            InsertShared& ish) {
     using BB = BlockBits<B>;
+    uint32_t* s_nb = ish.nb;
+    if (threadIdx.x == 0) ish.sum = 0;
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e)
         if (threadIdx.x == (unsigned)e && e < a.n_out) {
@@ -1447,6 +1456,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
     // with more warps than segments, the ways-th part of every segment's
     // batches goes to a different warp (more gathers in flight)
     const int64_t ways = max((int64_t)1, n_warps / a.total_warps);
+    unsigned long long bsec = 0;  // per lane (with a.insert_bsec)
 
     for (int64_t t = gw; t < a.total_warps * ways; t += n_warps) {
         const int64_t s = t % a.total_warps;
@@ -1462,6 +1472,24 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
                 live[i] = idx < cnt;
                 live_mask[i] = __ballot_sync(0xFFFFFFFFu, live[i]);
                 r[i] = live[i] ? ld_once(ids + idx) : 0u;
+            }
+            if (a.insert_bsec) {
+                // build sectors holding a survivor: rows ascend with the slot (i, then
+                // lane), so a row counts when its sector differs from the previous
+                // slot's row's -- the slot before `base` is ids[base - 1], or none at
+                // the segment's start (segments hold whole sectors)
+                const uint32_t before = base > 0 ? ld_once(ids + base - 1) : 0xFFFFFFFFu;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, r[i], 1);
+                    const uint32_t wrap = __shfl_sync(0xFFFFFFFFu, r[i > 0 ? i - 1 : 0], 31);
+                    const uint32_t prev = lane > 0 ? up : (i > 0 ? wrap : before);
+                    if (live[i])
+                        for (int c = 0; c < a.n_bcols; ++c) {
+                            const uint32_t shc = a.bcol[c].dtype == 0 ? 3u : 2u;
+                            bsec += (r[i] >> shc) != (prev >> shc);
+                        }
+                }
             }
 #pragma unroll
             for (int e = 0; e < kMaxOut; ++e) {
@@ -1523,6 +1551,12 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
             }
         }
     }
+    if (a.insert_bsec) {  // (the same for every thread of the CTA)
+        bsec = __reduce_add_sync(0xFFFFFFFFu, (unsigned)bsec);
+        if (lane == 0) warp_to_cta(&ish.sum, bsec);
+        __syncthreads();
+        if (threadIdx.x == 0) cta_to_global(&ish.sum, a.stats + 1);
+    }
 }
 
 // A backward visit that probes nothing (a source of the reversed DAG) keeps
@@ -1565,9 +1599,9 @@ __global__ void __launch_bounds__(512) pt_pass_through_kernel(const VisitArgs a,
 
 template <int B, int KT>
 __global__ void __launch_bounds__(512) pt_insert_kernel(const VisitArgs a, const FilterCfg f) {
-    __shared__ uint32_t s_nb[kMaxOut];
+    __shared__ InsertShared ish;
     grid_dependency_wait();
-    insert_part<B, KT>(a, f, blockIdx.x, gridDim.x, s_nb);
+    insert_part<B, KT>(a, f, blockIdx.x, gridDim.x, ish);
     allow_dependents();
 }
 
@@ -1575,7 +1609,7 @@ template <int B, int KT>
 __global__ void __launch_bounds__(512)
     pt_insert_batch_kernel(const VisitArgs* visits, const BatchTask* task_base, const int32_t* range,
                            const int32_t parts, const FilterCfg f) {
-    __shared__ uint32_t s_nb[kMaxOut];
+    __shared__ InsertShared ish;
     __shared__ __align__(16) VisitArgs s_a;
     const BatchTask* tasks = task_base + range[0];
     const int32_t n = range[1];
@@ -1583,7 +1617,7 @@ __global__ void __launch_bounds__(512)
         const BatchTask task = tasks[t];
         load_visit(s_a, visits + task.visit);
         __syncthreads();
-        insert_part<B, KT>(s_a, f, task.part, parts, s_nb);
+        insert_part<B, KT>(s_a, f, task.part, parts, ish);
         __syncthreads();
     }
 }

@@ -125,6 +125,7 @@ struct pt_ctx {
     int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
     void* meta[2] = {nullptr, nullptr};
     size_t meta_bytes = 0;
+    bool fold_through = false;  // set while a transfer run enqueues both passes
     int64_t seg_cap = 0;
 
     int scan_threads = 256;
@@ -457,6 +458,22 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
         a.ids = ctx->ids[p][v];
         a.seg_count = ctx->seg[p][v];
     }
+    // inside one transfer run, a table whose backward visit passes its forward
+    // survivors through has no backward scan: its forward scan zeroes the
+    // backward filters' previous words, and its backward insert counts the
+    // build sectors
+    if (ctx->fold_through && ctx->schedule == PT_SCHEDULE_TRANSFER) {
+        const int bv = ctx->vidx[1][v];
+        const Visit* b = bv >= 0 ? &ctx->visits[1][bv] : nullptr;
+        if (p == 0 && b && b->pass_through && a.n_out + (int)b->out_edges.size() <= pt::kMaxOut) {
+            for (int e : b->out_edges) {
+                pt::BuildEdge& be = a.out[a.n_out + a.n_clear_extra++];
+                be.filter = ctx->filt[1][e];
+                be.nblocks = ctx->nblocks[1] + e;
+            }
+        }
+        if (p == 1 && vis.pass_through) a.insert_bsec = 1;
+    }
 }
 
 // Compute every visit's scan shape and raise the kernels' dynamic shared
@@ -619,6 +636,7 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
                 ea.ids = nullptr;
                 ea.seg_count = nullptr;
                 ea.n_out = 0;
+                ea.n_clear_extra = 0;
                 ea.n_bcols = 0;
                 ea.count = ctx->early_count[p] + v;
                 if ((s1 = record_event(ctx, 0, fs, p, v)) != PT_OK) return s1;
@@ -636,15 +654,18 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         // ends (they wait for its results on the device); not between the event
         // records of a timed run
         const bool pdl = ctx->pdl && !ctx->timing;
-        if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
-        if (vis.pass_through)
-            PT_CUDA(ctx, pt::launch_pass_through(a, ctx->fcfg, ctx->num_sms * 2, st, pdl));
-        else if (p == 1 && vis.list)
-            PT_CUDA(ctx, pt::launch_probe_list(a, ctx->fcfg, vis.list_grid, vis.list_smem, st, pdl));
-        else
-            PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st, pdl));
-        if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
-        ctx->launches++;
+        // (a pass-through visit folded into its forward scan and its insert launches nothing here)
+        if (!(vis.pass_through && a.insert_bsec)) {
+            if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
+            if (vis.pass_through)
+                PT_CUDA(ctx, pt::launch_pass_through(a, ctx->fcfg, ctx->num_sms * 2, st, pdl));
+            else if (p == 1 && vis.list)
+                PT_CUDA(ctx, pt::launch_probe_list(a, ctx->fcfg, vis.list_grid, vis.list_smem, st, pdl));
+            else
+                PT_CUDA(ctx, pt::launch_scan(a, ctx->fcfg, sh.grid, sh.block, sh.smem, st, pdl));
+            if ((s1 = record_event(ctx, 0, st, p, v)) != PT_OK) return s1;
+            ctx->launches++;
+        }
         if (a.n_out > 0) {
             // the scan above zeroed the previous run's filter words; the insert sizes
             // the filters from the survivor count and sets their bits.  256-thread
@@ -1104,9 +1125,18 @@ pt_status pt_run_backward(pt_ctx* ctx) {
     return PT_OK;
 }
 
+// Both passes of a transfer, with pass-through visits folded (see
+// fill_visit_args); the flag is set only while they are enqueued.
+struct FoldThrough {
+    pt_ctx* ctx;
+    explicit FoldThrough(pt_ctx* c) : ctx(c) { ctx->fold_through = true; }
+    ~FoldThrough() { ctx->fold_through = false; }
+};
+
 pt_status pt_run_transfer(pt_ctx* ctx) {
     pt_status st = require_plan(ctx);
     if (st != PT_OK) return st;
+    FoldThrough fold(ctx);
     if (!ctx->graph_mode) {
         st = pt_run_forward(ctx);
         if (st != PT_OK) return st;

@@ -53,6 +53,18 @@ def collect(s, w):
     return out
 
 
+def folded(s, w):
+    """Tables whose backward visit passes its forward survivors through (no
+    incoming filter, some outgoing): inside a transfer run no scan-kind kernel
+    launches for them (the forward scan and the backward insert do its work)."""
+    out = set()
+    for v in range(w.n_tables):
+        st = s.stats(1, v)
+        if st is not None and st["n_in"] == 0 and st["n_out"] > 0:
+            out.add(v)
+    return out
+
+
 def run_gpu(w, **kw):
     s = session_for(w, **kw)
     try:
