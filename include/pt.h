@@ -197,7 +197,11 @@ pt_status pt_run_backward(pt_ctx* ctx);
 
 /* pt_run_forward then pt_run_backward as one call.  When the context's
  * graph mode is on (pt_set_graph_mode), the first call captures both
- * passes into a CUDA graph and later calls replay it. */
+ * passes into a CUDA graph and later calls replay it.  Results equal the
+ * two separate calls; one launch fewer per table whose backward visit
+ * probes nothing (its forward survivors pass through): its forward scan
+ * zeroes that visit's filters of the previous run and its backward insert
+ * counts the build sectors, so no scan-kind kernel launches for it. */
 pt_status pt_run_transfer(pt_ctx* ctx);
 
 /* 1 = capture the transfer into a CUDA graph on first pt_run_transfer and
