@@ -151,6 +151,7 @@ cudaError_t launch_probe_first(const VisitArgs& a, const FilterCfg& f, uint32_t*
                                int32_t smem_words, int32_t gate_words, int32_t gate, int grid, int block,
                                size_t smem, cudaStream_t s);
 int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem);
+int insert_max_ctas_per_sm(int block_bits, int block);  // resident insert CTAs of `block` threads
 // Parts a batched first probe of a visit of n rows is split into (host and
 // device agree on it): about kFirstTilesPerPart tiles each.
 constexpr int64_t kFirstTilesPerPart = 1024;

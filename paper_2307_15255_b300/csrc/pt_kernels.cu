@@ -1731,6 +1731,18 @@ int probe_first_max_ctas_per_sm(int block_bits, int block, size_t smem) {
     return n < m ? n : m;
 }
 
+int insert_max_ctas_per_sm(int block_bits, int block) {
+    int n = 0, m = 0;
+    if (block_bits == 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_insert_kernel<512, 4>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_insert_kernel<512, 0>, block, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pt_insert_kernel<256, 4>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pt_insert_kernel<256, 0>, block, 0);
+    }
+    return n < m ? n : m;
+}
+
 cudaError_t launch_pass_through(const VisitArgs& a, const FilterCfg& f, int grid, cudaStream_t s, bool pdl) {
     return launch_ex(pt_pass_through_kernel, 1, pdl, grid, 512, 0, s, a, f);
 }
