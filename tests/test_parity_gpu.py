@@ -396,6 +396,21 @@ def test_join_count_star_forest_and_one_way(oracle_lib):
         assert ei.value.status == P.PT_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("bpk,k,B", [(16, 4, 256), (10, 7, 512), (12, 3, 256)])
+def test_many_rows_into_a_tiny_filter(oracle_lib, bpk, k, B):
+    # 300k fact rows whose foreign key takes one of 12 values: the fact table's
+    # backward filter for the 12-row dimension has one or two blocks and is
+    # built from every surviving fact row (the insert builds a filter that
+    # small in each CTA's shared memory first, then ORs it into the filter)
+    rng = np.random.default_rng(21 + k)
+    nd, nf = 12, 300_000
+    d = np.arange(nd, dtype=np.int64) * 3 + 1
+    D = W.Table("D", nd, [d], ["id"], W.bitmap_from_rows(nd, [0, 2, 3, 5, 7, 11]))
+    F = W.Table("F", nf, [d[rng.integers(0, nd, nf)]], ["fk"], None)
+    w = W.Workload("tiny", [F, D], [W.Edge(0, (0,), 1, (0,))], bpk, k, B, 0)
+    _check(w, oracle_lib)
+
+
 @pytest.mark.parametrize("graph", [False, True])
 def test_transfer_and_separate_passes_alternate(oracle_lib, graph):
     # a transfer run folds the fact table's pass-through backward visit (its
