@@ -1432,6 +1432,7 @@ struct InsertShared {
     uint32_t nb[kMaxOut];    // this run's filter sizes
     unsigned long long sum;  // the CTA's build sectors (with a.insert_bsec; see warp_to_cta)
     uint32_t tiny[kMaxOut][kTinyWords];  // the CTA's part of each tiny filter
+    uint32_t repeat[kMaxOut];  // 1: more rows build the filter than the probe side has (see below)
 };
 
 // Part `part` of `nparts` of a visit's insert: warp w of the part takes the
@@ -1445,6 +1446,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
 #pragma unroll
     for (int e = 0; e < kMaxOut; ++e)
         if (threadIdx.x == (unsigned)e && e < a.n_out) {
+            ish.repeat[e] = (int64_t)*a.count > a.out[e].probe_rows;
             if (a.insert_sizes) {
                 // the scan zeroed the previous run's words; this run's size, from the count
                 // (the size rule with the block size known here: a shift, not a division)
@@ -1517,6 +1519,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
                 const BuildEdge& be = a.out[e];
                 const bool dedup = a.n > be.probe_rows;
                 const bool tiny = s_nb[e] * BB::WPB <= (uint32_t)kTinyWords;  // (warp-uniform)
+                const bool repeat = ish.repeat[e] != 0;
                 uint64_t h[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) h[i] = live[i] ? edge_hash(be.col[0], be.col[1], be.ncols, r[i], seed) : 0ull;
@@ -1569,13 +1572,30 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
                                     m[u] |= m[t];
                                     m[t] = 0;
                                 }
+                        if (repeat) {
+                            // more rows than the probe side has, so keys repeat, and a skewed
+                            // one many times: a repeated key usually finds its bits set
+                            // already, so read its words (from L2, where the atomics land) and
+                            // skip the atomics that would change nothing, so that a hot key's
+                            // block is not hit by one atomic per row (with fewer rows the
+                            // extra read only adds latency: 18 -> 20 us on a 20k-row build)
+                            uint32_t cur[KT > 0 ? KT : 1];
 #pragma unroll
-                        for (int t = 0; t < KT; ++t)
-                            if (m[t]) atomicOr(blk + w[t], m[t]);
+                            for (int t = 0; t < KT; ++t) cur[t] = m[t] ? __ldcg(blk + w[t]) : 0u;
+#pragma unroll
+                            for (int t = 0; t < KT; ++t)
+                                if (m[t] & ~cur[t]) atomicOr(blk + w[t], m[t] & ~cur[t]);
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < KT; ++t)
+                                if (m[t]) atomicOr(blk + w[t], m[t]);
+                        }
                     } else {
                         for (int t = 0; t < k; ++t) {
                             const uint32_t at = mad_lo((uint32_t)t, h2, lo);
-                            atomicOr(blk + mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB), 1u << (at & 31));
+                            uint32_t* wp = blk + mul_hi(mad_lo(at, BB::SCALE, 0u), BB::WPB);
+                            const uint32_t bit = 1u << (at & 31);
+                            if (!repeat || !(__ldcg(wp) & bit)) atomicOr(wp, bit);
                         }
                     }
                 }
