@@ -411,6 +411,21 @@ def test_many_rows_into_a_tiny_filter(oracle_lib, bpk, k, B):
     _check(w, oracle_lib)
 
 
+@pytest.mark.parametrize("bpk,k,B", [(16, 4, 256), (12, 3, 256), (10, 7, 512)])
+def test_more_building_rows_than_probe_rows_skewed(oracle_lib, bpk, k, B):
+    # 400k fact rows with Zipf(1.1) foreign keys into a 20k-row dimension: the
+    # fact table's backward build has 20 times more rows than the dimension,
+    # so the insert reads each key's words and skips atomics that would set
+    # nothing new (the filter is far larger than the shared-memory copies)
+    rng = np.random.default_rng(31 + k)
+    nd, nf = 20_000, 400_000
+    d = rng.permutation(nd).astype(np.int64) * 5 - 7
+    D = W.Table("D", nd, [d], ["id"], W.bitmap_from_bools(rng.random(nd) < 0.6))
+    F = W.Table("F", nf, [d[W.fk_rows(rng, nd, nf, 1.1)]], ["fk"], None)
+    w = W.Workload("skew", [F, D], [W.Edge(0, (0,), 1, (0,))], bpk, k, B, 0)
+    _check(w, oracle_lib)
+
+
 @pytest.mark.parametrize("graph", [False, True])
 def test_transfer_and_separate_passes_alternate(oracle_lib, graph):
     # a transfer run folds the fact table's pass-through backward visit (its
