@@ -1421,12 +1421,13 @@ __global__ void __launch_bounds__(512)
 // ---------------------------------------------------------------------------
 // 3. insert the survivors' outgoing keys
 // ---------------------------------------------------------------------------
-// A filter of at most kTinyWords words is built in each CTA's shared memory
-// and then ORed into the global one word by word: many rows inserting into a
-// few blocks (a foreign key into a tiny table, whose probe side caps the
-// filter's size) otherwise pile thousands of atomics onto one L2 line, which
-// serialises them (measured: D1's backward insert into N's 2-block filter,
-// 7373 rows, took 11 us more than its CTAs ran).
+// A filter of at most kTinyWords words that more rows build than its probe
+// side has is built in each CTA's shared memory and then ORed into the global
+// one word by word: many rows inserting into a few blocks (a foreign key into
+// a tiny table, whose probe side caps the filter's size) otherwise pile
+// thousands of atomics onto one L2 line, which serialises them (measured: D1's
+// backward insert into N's 2-block filter, 7373 rows, took 11 us more than its
+// CTAs ran).  A few rows into a small filter go straight to it.
 constexpr int kTinyWords = 128;
 struct InsertShared {
     uint32_t nb[kMaxOut];    // this run's filter sizes
@@ -1461,10 +1462,11 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
     __syncthreads();
     // tiny filters: this CTA's shared copies start empty
     bool any_tiny = false;
-    for (int e = 0; e < a.n_out; ++e) any_tiny |= s_nb[e] * BB::WPB <= (uint32_t)kTinyWords;
+    auto tiny_edge = [&](int e) { return ish.repeat[e] != 0 && s_nb[e] * BB::WPB <= (uint32_t)kTinyWords; };
+    for (int e = 0; e < a.n_out; ++e) any_tiny |= tiny_edge(e);
     if (any_tiny) {
         for (int e = 0; e < a.n_out; ++e)
-            if (s_nb[e] * BB::WPB <= (uint32_t)kTinyWords)
+            if (tiny_edge(e))
                 for (uint32_t w = threadIdx.x; w < s_nb[e] * BB::WPB; w += blockDim.x) ish.tiny[e][w] = 0u;
         __syncthreads();
     }
@@ -1518,7 +1520,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
                 if (e >= a.n_out) break;
                 const BuildEdge& be = a.out[e];
                 const bool dedup = a.n > be.probe_rows;
-                const bool tiny = s_nb[e] * BB::WPB <= (uint32_t)kTinyWords;  // (warp-uniform)
+                const bool tiny = tiny_edge(e);  // (warp-uniform)
                 const bool repeat = ish.repeat[e] != 0;
                 uint64_t h[4];
 #pragma unroll
@@ -1607,7 +1609,7 @@ __device__ __forceinline__ void insert_part(const VisitArgs& a, const FilterCfg&
         __syncthreads();
         for (int e = 0; e < a.n_out; ++e) {
             const uint32_t words = s_nb[e] * BB::WPB;
-            if (words > (uint32_t)kTinyWords) continue;
+            if (!tiny_edge(e)) continue;
             for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
                 const uint32_t v = ish.tiny[e][w];
                 if (v) atomicOr(a.out[e].filter + w, v);
