@@ -568,16 +568,28 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
     std::stable_sort(seq.begin(), seq.end(), [&](const Visit* x, const Visit* y) {
         return ctx->lvl[p][x->table] < ctx->lvl[p][y->table];
     });
+    // Waits on events only across streams: on one stream, order already holds
+    // (every kernel a visit launches as a programmatic dependent waits for the
+    // kernel before it at its start, so each waits, in turn, for all earlier
+    // ones), and a wait on an event of the same stream would turn the
+    // programmatic edge from the kernel before into a full one (measured
+    // between consecutive visits of one stream: about 4.5 µs from the end of
+    // one kernel's last CTA to the next one's first, against 1.5 µs)
+    bool joined[pt_ctx::kAux] = {};
     for (const Visit* vp : seq) {
         const Visit& vis = *vp;
         const int v = vis.table;
-        cudaStream_t st = ctx->aux[ctx->slot[p][v] % ctx->streams];
-        PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
+        const int sv = ctx->slot[p][v] % ctx->streams;
+        cudaStream_t st = ctx->aux[sv];
+        if (!joined[sv]) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
+        joined[sv] = true;
         // the visits that build its filters in this pass (filters of an earlier
         // pass are complete when this one forks from the context stream)
         const bool same_pass = ctx->fpass[p] == p;
         if (same_pass)
-            for (int e : vis.in_edges) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[p][ctx->bld[p][e]], 0));
+            for (int e : vis.in_edges)
+                if (ctx->slot[p][ctx->bld[p][e]] % ctx->streams != sv)
+                    PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[p][ctx->bld[p][e]], 0));
         const ScanShape& sh = vis.shape;
         pt::VisitArgs a;
         fill_visit_args(ctx, p, vis, sh, a);
@@ -650,7 +662,7 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
                 a.in_bits = ctx->mid2[v];
                 a.level_lo = vis.early_level;
             }
-            PT_CUDA(ctx, cudaStreamWaitEvent(st, done, 0));
+            if (fs != st) PT_CUDA(ctx, cudaStreamWaitEvent(st, done, 0));
         }
         // a visit's kernels may start while the kernel before them on their stream
         // ends (they wait for its results on the device); not between the event
