@@ -597,15 +597,23 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         if (vis.first && ctx->first_probe) {
             // in the default probe order the first probe tests a filter of one of
             // the lowest-level builders: it waits for those only, on its own
-            // stream; in the other orders it may be any builder's
-            cudaStream_t fs = ctx->streams > 1 ? ctx->fstream[v] : st;
-            PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
+            // stream; in the other orders it may be any builder's.  When every
+            // builder is at that level (a visit with one incoming edge), the visit's
+            // own stream, which waits for them anyway, takes it: no event between
+            // the builders and the pass, nor between the pass and the scan
+            int32_t lmin = INT32_MAX;
+            bool all_lowest = true;
             if (same_pass) {
-                int32_t lmin = INT32_MAX;
                 for (int e : vis.in_edges) lmin = std::min(lmin, ctx->lvl[p][ctx->bld[p][e]]);
-                for (int e : vis.in_edges)
-                    if (ctx->fcfg.probe_order != 0 || ctx->lvl[p][ctx->bld[p][e]] == lmin)
-                        PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->bld[p][e]], 0));
+                for (int e : vis.in_edges) all_lowest = all_lowest && ctx->lvl[p][ctx->bld[p][e]] == lmin;
+            }
+            cudaStream_t fs = ctx->streams > 1 && !all_lowest ? ctx->fstream[v] : st;
+            if (fs != st) {
+                PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->pass_ev[p], 0));
+                if (same_pass)
+                    for (int e : vis.in_edges)
+                        if (ctx->fcfg.probe_order != 0 || ctx->lvl[p][ctx->bld[p][e]] == lmin)
+                            PT_CUDA(ctx, cudaStreamWaitEvent(fs, ctx->vev[p][ctx->bld[p][e]], 0));
             }
             // and for the first-probe passes of lower-level visits: those lead to
             // this visit's higher-level builders, and a first-probe pass over a
