@@ -125,7 +125,8 @@ struct pt_ctx {
     int64_t* nblocks[2] = {nullptr, nullptr};            // [edge]
     void* meta[2] = {nullptr, nullptr};
     size_t meta_bytes = 0;
-    bool fold_through = false;  // set while a transfer run enqueues both passes
+    bool in_transfer = false;  // set while a transfer run enqueues both passes (see InTransfer)
+    bool chain_ok = false;     // every backward visit's table has a forward visit (pt_plan)
     int insert_fit = 4;         // resident 256-thread insert CTAs per SM (prepare_shapes)
     int64_t seg_cap = 0;
 
@@ -463,7 +464,7 @@ void fill_visit_args(pt_ctx* ctx, int p, const Visit& vis, const ScanShape& sh, 
     // survivors through has no backward scan: its forward scan zeroes the
     // backward filters' previous words, and its backward insert counts the
     // build sectors
-    if (ctx->fold_through && ctx->schedule == PT_SCHEDULE_TRANSFER) {
+    if (ctx->in_transfer && ctx->schedule == PT_SCHEDULE_TRANSFER) {
         const int bv = ctx->vidx[1][v];
         const Visit* b = bv >= 0 ? &ctx->visits[1][bv] : nullptr;
         if (p == 0 && b && b->pass_through && a.n_out + (int)b->out_edges.size() <= pt::kMaxOut) {
@@ -559,8 +560,18 @@ pt_status record_event(pt_ctx* ctx, int kind, cudaStream_t st, int pass, int tab
 
 pt_status enqueue_pass(pt_ctx* ctx, int p) {
     if (!ctx->shapes_ready) return fail(ctx, PT_ERR_STATE, "launch shapes not prepared");
-    PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
-    PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
+    // Inside one transfer run the backward pass does not wait for the whole
+    // forward pass: a backward visit reads only its own table's forward results
+    // (survivors, row ids, the hashes its forward inserts kept, the filters its
+    // forward scan zeroed) and the filters its backward builders make, so it
+    // waits for its forward visit and those builders, and the pass-1 counters
+    // are zeroed with the pass-0 ones before either pass starts
+    const bool chained = ctx->in_transfer && ctx->schedule == PT_SCHEDULE_TRANSFER && ctx->chain_ok;
+    if (!(chained && p == 1)) {
+        PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
+        if (chained) PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[1], 0, ctx->meta_bytes, ctx->stream));
+        PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
+    }
     // enqueue by level (then visiting order): a stream never holds a visit
     // behind one of a higher level, which would delay it for nothing
     std::vector<const Visit*> seq;
@@ -581,8 +592,12 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         const int v = vis.table;
         const int sv = ctx->slot[p][v] % ctx->streams;
         cudaStream_t st = ctx->aux[sv];
-        if (!joined[sv]) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
-        joined[sv] = true;
+        if (chained && p == 1) {
+            if (ctx->slot[0][v] % ctx->streams != sv) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->vev[0][v], 0));
+        } else {
+            if (!joined[sv]) PT_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pass_ev[p], 0));
+            joined[sv] = true;
+        }
         // the visits that build its filters in this pass (filters of an earlier
         // pass are complete when this one forks from the context stream)
         const bool same_pass = ctx->fpass[p] == p;
@@ -702,8 +717,11 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
         }
         PT_CUDA(ctx, cudaEventRecord(ctx->vev[p][v], st));
     }
-    // join: the pass is complete on the context stream
-    for (const Visit& vis : ctx->visits[p]) PT_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->vev[p][vis.table], 0));
+    // join: the pass is complete on the context stream (in a chained transfer,
+    // both passes, after the backward one)
+    if (chained && p == 0) return PT_OK;
+    for (int q = chained ? 0 : p; q <= p; ++q)
+        for (const Visit& vis : ctx->visits[q]) PT_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->vev[q][vis.table], 0));
     return PT_OK;
 }
 
@@ -940,6 +958,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
             vis.list = ctx->has_edge[vis.table];
             vis.pass_through = vis.list && vis.in_edges.empty() && !vis.out_edges.empty();
         }
+    // a transfer run may chain each backward visit onto its table's forward visit
+    ctx->chain_ok = !one_hop;
+    for (const Visit& vis : ctx->visits[1]) ctx->chain_ok = ctx->chain_ok && ctx->vidx[0][vis.table] >= 0;
 
     // streams and events for concurrent visits (level = longest path from a
     // source of the pass's DAG)
@@ -982,6 +1003,9 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
                         pref = ctx->slot[p][b];
                     }
                 }
+                // a backward visit with no builder in its pass continues its forward
+                // visit's stream (it reads that visit's results)
+                if (pref < 0 && p == 1 && !one_hop && ctx->vidx[0][v] >= 0) pref = ctx->slot[0][v];
                 int sl = pref >= 0 && !taken[pref] ? pref : -1;
                 for (int i = 0; sl < 0 && i < pt_ctx::kAux; ++i)
                     if (!taken[i]) sl = i;
@@ -1150,16 +1174,16 @@ pt_status pt_run_backward(pt_ctx* ctx) {
 
 // Both passes of a transfer, with pass-through visits folded (see
 // fill_visit_args); the flag is set only while they are enqueued.
-struct FoldThrough {
+struct InTransfer {
     pt_ctx* ctx;
-    explicit FoldThrough(pt_ctx* c) : ctx(c) { ctx->fold_through = true; }
-    ~FoldThrough() { ctx->fold_through = false; }
+    explicit InTransfer(pt_ctx* c) : ctx(c) { ctx->in_transfer = true; }
+    ~InTransfer() { ctx->in_transfer = false; }
 };
 
 pt_status pt_run_transfer(pt_ctx* ctx) {
     pt_status st = require_plan(ctx);
     if (st != PT_OK) return st;
-    FoldThrough fold(ctx);
+    InTransfer fold(ctx);
     if (!ctx->graph_mode) {
         st = pt_run_forward(ctx);
         if (st != PT_OK) return st;
