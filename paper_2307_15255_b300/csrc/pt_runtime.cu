@@ -568,8 +568,8 @@ pt_status enqueue_pass(pt_ctx* ctx, int p) {
     // are zeroed with the pass-0 ones before either pass starts
     const bool chained = ctx->in_transfer && ctx->schedule == PT_SCHEDULE_TRANSFER && ctx->chain_ok;
     if (!(chained && p == 1)) {
-        PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes, ctx->stream));
-        if (chained) PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[1], 0, ctx->meta_bytes, ctx->stream));
+        // (the two passes' counters are adjacent in the arena: one memset for both)
+        PT_CUDA(ctx, cudaMemsetAsync(ctx->meta[p], 0, ctx->meta_bytes * (chained ? 2 : 1), ctx->stream));
         PT_CUDA(ctx, cudaEventRecord(ctx->pass_ev[p], ctx->stream));
     }
     // enqueue by level (then visiting order): a stream never holds a visit
@@ -1087,7 +1087,7 @@ pt_status pt_plan(pt_ctx* ctx, int32_t* order_out, int64_t* mem_bytes_out) {
     // u64, first-probe edge [T] i32
     ctx->meta_bytes = align_up((size_t)T * 8 + (size_t)T * 24 + (size_t)T * 8 + (size_t)T * 4);
     size_t o_meta[2], o_nblocks[2];
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < 2; ++p) {  // adjacent: a chained transfer zeroes both with one memset
         o_meta[p] = off;
         off += ctx->meta_bytes;
     }
