@@ -449,10 +449,34 @@ def test_transfer_and_separate_passes_alternate(oracle_lib, graph):
         assert folded(s, w)
 
 
-@pytest.mark.parametrize("pdl,streams,graph", [(False, 3, False), (False, 1, True), (True, 1, False), (True, 3, True)])
+@pytest.mark.parametrize("streams", [1, 2, 3])
+def test_random_graphs_with_one_way_edges_on_few_streams(oracle_lib, streams):
+    # a transfer run chains each backward visit onto its own forward visit and
+    # its backward builders only; one-way edges build in one pass, so some
+    # visits have builders in one pass and not the other
+    import dataclasses
+    from _gpu import assert_same, collect, session_for
+    from paper_2307_15255_b300 import pt as P
+    rng = np.random.default_rng(77 + streams)
+    for seed in range(10):
+        w = W.random_tiny(5200 + 10 * streams + seed, 3 + seed % 4, max_rows=3000, domain=40,
+                          acyclic=seed % 2 == 0, composite_prob=0.25)
+        w = dataclasses.replace(w, edges=[dataclasses.replace(e, flags=int(rng.random() < 0.3)) for e in w.edges])
+        want = oracle_lib.transfer(w)
+        with session_for(w, graph=seed % 2 == 1) as s:
+            P.pt_set_streams(s.ctx, streams)
+            for _ in range(2):
+                s.run()
+            assert_same(collect(s, w), want, w)
+
+
+@pytest.mark.parametrize("pdl,streams,graph", [(False, 3, False), (False, 1, True), (True, 1, False), (True, 3, True),
+                                               (True, 2, True), (True, 2, False)])
 def test_dependent_launches_and_streams(oracle_lib, pdl, streams, graph):
     # programmatic dependent launches on or off, every visit on one stream or
-    # spread over three, direct launches or a captured graph: the same results
+    # spread over two or three (visits whose planned streams fold onto one then
+    # share it: the waits between them are left to stream order), direct
+    # launches or a captured graph: the same results
     from _gpu import assert_same, collect, session_for
     from paper_2307_15255_b300 import pt as P
     w = W.snowflake(scale=0.25, int64=True, composite=True, zipf=1.1, bits_per_key=16)
